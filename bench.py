@@ -1,0 +1,353 @@
+"""Benchmark of the fused chi^2 + gradient evaluation.
+
+Default workload: reactor8_1000x16384 -- 1000 bins in 0.5-15 MeV x 16384
+Gauss-Legendre nodes x 8 baselines (131,072,000 probability evaluations per
+step), parameters perturbed by +-5 %, Poisson chi^2, per-baseline spectra and
+the four-parameter gradient.  One step = one evaluation of the whole chain
+(parameter prep, fused phase/probability/weight/bin-sum kernel, chi^2 and
+gradient epilogue) in the double-float-phase mixed precision.
+
+Prints one JSON line (rank 0).  Under torchrun every rank evaluates its own
+replica (its own pseudo-data seed): units are independent, there is no
+data-path collective, and the timing is the max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1804_07682_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "χ²+grad evals/s and Gpoints/s vs plain FP64 GPU chain at ≤1e-6 rel err; % roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 issue peak: 152 SMs x 128 FP32 lanes per clock x 2070 MHz (maximum SM clock)
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
+    """Algorithmic FP32 operations (FMA = 1) of the fused kernel per energy node.
+
+    Per (node, baseline): double-float phase and reduction mod pi 2 x 10,
+    sin/cos polynomials 2 x 13, angle addition 2, three squares, three
+    weighted sums (46 + 2 + 3 + 3 = 54); gradient: cos of the sum 2, three
+    sin*cos products and three weighted sums (8); spectra: P_r 3 + Kahan
+    product-sum 4 (7).  Per node: combined P 3 + Kahan 4; gradient: tangent
+    combinations 10 + four Kahan product-sums 16.
+    """
+    per_r = 54 + (8 if grad else 0) + (7 if spec else 0)
+    per_node = 7 + (26 if grad else 0)
+    return nL * per_r + per_node
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % index) if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d_%d.csv" % (index, os.getpid())
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([float(r[1]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() in ("active", "1")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def reduce_max(dist, x, device):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- reference arm --
+def reference_arm(args):
+    """The oracle, as it stands, timed on the host cores (bounded sample per step)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+
+    w = wl.ALL[args.workload]()
+    nb = args.ref_bins
+    edges = w.edges[: nb + 1]
+    data = np.full(nb, 100.0)
+    N = 1.0
+    th = w.theta[0]
+
+    def step():
+        return oracle.chain(edges, w.nodes_per_bin, w.L, th, N, data, w.kind, e_scale=w.e_scale)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    frac = nb / w.nbins
+    evals = frac / dt
+    line = {"impl": "reference", "metric": METRIC, "value": evals, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / frac, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "bins_per_step": nb, "points_per_eval": w.points_per_eval()},
+            "gpoints_per_s": evals * w.points_per_eval() / 1e9,
+            "cpu_baseline": {"value": evals, "unit": "evals/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "%d of %d bins per step (x%d nodes x%d baselines), scaled to one full eval"
+                                       % (nb, w.nbins, w.nodes_per_bin, w.nL)},
+            "e2e": {"value": evals, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- ours --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="reactor8_1000x16384")
+    ap.add_argument("--prec", default="ff", choices=["ff", "f64phase", "fp64"])
+    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 chain comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None)
+    ap.add_argument("--ref-bins", type=int, default=16)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    from paper_1804_07682_gb300 import api
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    device = torch.device("cuda", local)
+    w = wl.ALL[args.workload]()
+    if w.node_counts is not None or w.n_datasets > 1:
+        raise SystemExit("bench.py times the single-point reactor workloads; use --workload reactor8_1000x16384")
+    stream = torch.cuda.current_stream()
+
+    # Configuration stage: plan, Asimov truth from the library itself (normalised
+    # to 1e5 events), Poisson pseudo-data with a per-rank seed.
+    plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, norm=1.0, e_scale=w.e_scale, prec=args.prec,
+                    kind=w.kind, with_plain=not args.no_plain)
+    truth = plan.params_tensor(w.truth)
+    dummy = torch.ones(w.nbins, dtype=torch.float64, device=device)
+    m = plan.eval(truth, dummy, grad=False, mu=True)["mu"][0]
+    N = wl.TOTAL_EVENTS / float(m.sum())
+    plan.close()
+    plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, norm=N, e_scale=w.e_scale, prec=args.prec,
+                    kind=w.kind, with_plain=not args.no_plain)
+    mu_truth = (m * N).cpu().numpy()
+    data_np = wl.poisson_data(mu_truth, w.data_seed + 1000 * rank)
+    data = torch.as_tensor(data_np, device=device)
+    params = plan.params_tensor(w.theta)
+    if args.tuning:
+        plan.tuning = args.tuning
+    elif not args.no_autotune:
+        plan.autotune(params, data, reps=5)
+    out = {"chi2": torch.empty(1, dtype=torch.float64, device=device),
+           "grad": torch.empty(1, 4, dtype=torch.float64, device=device),
+           "spectra": torch.empty(1, w.nL, w.nbins, dtype=torch.float64, device=device)}
+
+    def step():
+        plan.eval(params, data, grad=True, spectra=True, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.status()
+    launches_per_step = plan.launches
+
+    # Timed region: K evaluations, events on the launching stream, kernel events inside the library.
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    plan.profile(True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    kern_ms, kern_n = plan.profile_read()
+    plan.profile(False)
+    clk = clocks.stop()
+    ms_total = reduce_max(dist, ms_total, device)
+    ms_step = ms_total / args.steps
+    evals_per_s = world * args.steps / (ms_total / 1e3)
+    points = w.points_per_eval()
+    kern_avg_ms = kern_ms / max(kern_n, 1)
+
+    # roofline of the fused kernel (ALU-bound: FP32 issue)
+    ops = fp32_ops_per_node(w.nL, True, True) * w.nbins * w.nodes_per_bin
+    achieved_tops = ops / (kern_avg_ms * 1e-3) / 1e12
+    peak_tops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    pk, pk_src = peaks()
+    hbm_bytes = 16 * w.nbins * w.nodes_per_bin
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
+                "frac": achieved_tops / peak_tops, "traffic": None,
+                "kernel": "k_fused_split (double-float phase, 8 baselines, gradient + spectra)",
+                "kernel_ms": kern_avg_ms, "ops_per_launch": ops,
+                "peak_note": "FP32 issue peak 152 SM x 128 lanes x 2070 MHz (FMA = 1 op)",
+                "hbm_frac": hbm_bytes / (kern_avg_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0),
+                "hbm_peak_src": pk_src}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    p_host = torch.as_tensor(w.theta.reshape(1, 4)).pin_memory().numpy()
+    d_host = torch.as_tensor(data_np).pin_memory().numpy()
+    c_host = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
+    g_host = torch.empty(1, 4, dtype=torch.float64).pin_memory().numpy()
+    s_host = torch.empty(1, w.nL, w.nbins, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(10, args.steps // 4)
+    for _ in range(3):
+        plan.eval_host(p_host, d_host, grad=True, chi2_out=c_host, grad_out=g_host, spectra_out=s_host)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.eval_host(p_host, d_host, grad=True, chi2_out=c_host, grad_out=g_host, spectra_out=s_host)
+    e2e_s = reduce_max(dist, time.perf_counter() - t0, device)
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": p_host.nbytes + d_host.nbytes,
+           "d2h_bytes_per_step": c_host.nbytes + g_host.nbytes + s_host.nbytes}
+
+    # plain FP64 chain on the same GPU, and the error of the timed path against it
+    plain = None
+    if not args.no_plain:
+        po = {"chi2": torch.empty(1, dtype=torch.float64, device=device),
+              "grad": torch.empty(1, 4, dtype=torch.float64, device=device),
+              "spectra": torch.empty(1, w.nL, w.nbins, dtype=torch.float64, device=device),
+              "mu": torch.empty(1, w.nbins, dtype=torch.float64, device=device)}
+        plan.eval(params, data, grad=True, spectra=True, mu=True, out=po, plain=True)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.plain_steps):
+            plan.eval(params, data, grad=True, spectra=True, mu=True, out=po, plain=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = reduce_max(dist, a0.elapsed_time(a1) / args.plain_steps, device)
+        mo = plan.eval(params, data, grad=True, spectra=True, mu=True)
+        torch.cuda.synchronize()
+        relerr = lambda a, b: float(((a - b).abs() / b.abs()).max())
+        plain = {"evals_per_s": world * 1e3 / plain_ms, "ms_per_step": plain_ms,
+                 "speedup": (world * 1e3 / plain_ms) and evals_per_s / (world * 1e3 / plain_ms),
+                 "max_rel_err": {"chi2": relerr(mo["chi2"], po["chi2"]), "mu": relerr(mo["mu"], po["mu"]),
+                                 "spectra": relerr(mo["spectra"], po["spectra"]),
+                                 "grad_normwise": float((mo["grad"] - po["grad"]).norm() / po["grad"].norm())}}
+
+    # CPU baseline: the oracle, as it stands, on a bounded sample (rank 0 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        nb = args.ref_bins
+        t0 = time.perf_counter()
+        oracle.chain(w.edges[: nb + 1], w.nodes_per_bin, w.L, w.theta[0], 1.0, np.full(nb, 100.0), w.kind)
+        dt = time.perf_counter() - t0
+        cpu = {"value": (nb / w.nbins) / dt, "unit": "evals/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": "%d of %d bins (x%d nodes x%d baselines, with gradient) in %.2f s, scaled to one eval"
+                         % (nb, w.nbins, w.nodes_per_bin, w.nL, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": evals_per_s, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+ff-phase" if args.prec == "ff" else args.prec, "data": "synthetic",
+                "config": {"workload": w.name, "bins": w.nbins, "nodes_per_bin": w.nodes_per_bin, "baselines": w.nL,
+                           "points_per_eval": points, "outputs": "chi2, 4-parameter gradient, 8 per-baseline spectra",
+                           "l2": "inputs larger than L2 (%d MB energy grid)" % (hbm_bytes >> 20),
+                           "tuning": plan.tuning, "parallelism": "replicas" if world > 1 else "single"},
+                "gpoints_per_s": evals_per_s * points / 1e9, "roofline": roofline, "plain_fp64_chain": plain,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

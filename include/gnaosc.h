@@ -1,0 +1,251 @@
+/*
+ * gnaosc.h -- C ABI of the GB300 oscillation-chain library (libgnaosc.so).
+ *
+ * The library evaluates the three-flavour vacuum electron-antineutrino
+ * survival probability on large energy arrays and the chain that consumes
+ * it: spectrum x oscillation weight, Gauss-Legendre integration per bin over
+ * one or more baselines, Pearson or Poisson chi^2 against data, the gradient
+ * of chi^2 with respect to (sin^2 theta12, sin^2 theta13, dm2_21, dm2_32,
+ * per-bin nuisances), batched parameter points with uneven grids, and batched
+ * Levenberg-Marquardt fits.
+ *
+ * Paper: "CUDA Support in GNA Data Analysis Framework" (arXiv:1804.07682).
+ * The probability is the paper's Sec. 4.1 vacuum formula with alpha = beta = e;
+ * the calls follow its transformation model (Sec. 2.1: read-only array
+ * inputs, scalar "variables", outputs allocated at the configuration stage,
+ * Sec. 4.2: all memory preallocated, inputs are views, the status of a GPU
+ * function is available on the host after the computation).
+ *
+ * Conventions for every call:
+ *   - Units: E in MeV, L in km, dm2 in eV^2.  The phase of pair (i,j) is
+ *     1266.932679419849 * dm2_ij * L / E rad (hbar c = 197.3269804 MeV fm);
+ *     dm2_31 = dm2_21 + dm2_32 (normal ordering).
+ *   - "device" pointers are CUDA global-memory pointers on the current
+ *     device, owned by the caller; "host" pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it and return;
+ *     argument errors are returned at once, device-side failures (including
+ *     bounded-wait timeouts) are reported by gna_plan_status().
+ *   - Evaluation calls use only the memory gna_plan_create() allocated;
+ *     the one call that allocates outside a plan is gna_gl_nodes (a
+ *     temporary of 16 n bytes, freed before it returns).
+ *   - No exception crosses the ABI.  Errors are gna_status codes; the text of
+ *     the last error of a plan is gna_plan_error(plan).
+ *   - Layouts are row-major C arrays; [a][b] means b varies fastest.
+ */
+#ifndef GNAOSC_H
+#define GNAOSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GNA_OK = 0,
+    GNA_EINVAL = 1,   /* bad argument value or NULL pointer */
+    GNA_ESHAPE = 2,   /* sizes inconsistent with the plan or out of range */
+    GNA_ENOMEM = 3,   /* device or pinned-host allocation failed (plan creation only) */
+    GNA_ECUDA = 4,    /* a CUDA runtime call failed */
+    GNA_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    GNA_ESTATE = 6    /* call not valid in the plan's current state */
+} gna_status;
+
+typedef enum {
+    GNA_FP64 = 0,           /* all arithmetic in double */
+    GNA_MIXED_F64PHASE = 1, /* phase and its reduction mod pi in double, the rest FP32 + Kahan */
+    GNA_MIXED_FFPHASE = 2   /* phase as an unevaluated sum of two floats (double-FP32), rest FP32 + Kahan */
+} gna_precision;
+
+typedef enum { GNA_PEARSON = 0, GNA_POISSON = 1 } gna_chi2_kind;
+
+/* Oscillation parameters of one point: the transformation's "variables". */
+typedef struct {
+    double s2_12;  /* sin^2 theta12 */
+    double s2_13;  /* sin^2 theta13 */
+    double dm2_21; /* eV^2 */
+    double dm2_32; /* eV^2 */
+} gna_osc;
+
+/* Configuration of a plan (host memory; copied by gna_plan_create). */
+typedef struct {
+    int nbins;                  /* >= 1 */
+    const double* edges;        /* host [nbins+1], MeV, strictly increasing, > 0 */
+    int nodes_per_bin;          /* Gauss-Legendre order of every point when node_counts == NULL; 1..65536 */
+    int npts;                   /* parameter points evaluated per call; >= 1 */
+    const int32_t* node_counts; /* host [npts] per-point order (each point its own grid), or NULL */
+    int nL;                     /* baselines, 1..16 */
+    const double* L;            /* host [nL], km, > 0 */
+    const double* Lweight;      /* host [nL] combination weights, or NULL for 1/L^2 normalised to sum 1 */
+    double norm;                /* N: mu_i = N (1 + eta_i) sum_r omega_r mu_r,i */
+    double e_scale;             /* spectrum S(E * e_scale): 1 for MeV, 1e-3 for GeV */
+    gna_precision prec;
+    gna_chi2_kind kind;
+    int max_datasets;           /* >= npts when each point has its own data row (fits); 0 = npts */
+    int flags;                  /* GNA_PLAN_* bits below */
+} gna_plan_desc;
+
+#define GNA_PLAN_WITH_PLAIN 1  /* also build the FP64 arrays and scratch of gna_chain_eval_plain */
+#define GNA_PLAN_FORCE_SPLIT 2 /* CTA tiles split each bin's nodes (default for >= 1024 nodes/bin) */
+#define GNA_PLAN_FORCE_BINS 4  /* one thread per bin (default for small or per-point grids) */
+
+/* Outputs of one evaluation (device pointers; any may be NULL except chi2). */
+typedef struct {
+    double* chi2;    /* [npts] */
+    double* grad;    /* [npts][4] d chi2 / d(s2_12, s2_13, dm2_21, dm2_32) */
+    double* grad_eta;/* [npts][nbins] d chi2 / d eta_i (needs eta) */
+    double* mu;      /* [npts][nbins] mu_i = N (1 + eta_i) M_i */
+    double* spectra; /* [npts][nL][nbins] per-baseline integrals mu_r,i = int_bin S(E) P_r(E) dE */
+} gna_outputs;
+
+typedef struct gna_plan gna_plan;
+
+/* ---------------------------------------------------------------------------
+ * gna_strerror: static text for a status code.  Never NULL.
+ */
+const char* gna_strerror(gna_status s);
+
+/* ---------------------------------------------------------------------------
+ * gna_gl_nodes: n-point Gauss-Legendre rule on [-1, 1] (nodes ascending,
+ * weights), computed by a device kernel (Newton iteration on the Legendre
+ * recurrence, FP64).  The rule is not in the paper; it is the integration
+ * step of the chain.  x, w: device [n].  n in 1..65536 else GNA_ESHAPE.
+ */
+gna_status gna_gl_nodes(int n, double* x, double* w, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gna_oscprob_ee: element-wise OscProb transformation, paper Sec. 4.1
+ * (P(nue_bar -> nue_bar), i.e. alpha = beta = e of the general formula, for
+ * which the Im term vanishes): P[r][k] = 1 - sum_{i>j} A_ij sin^2(phase_ij)
+ * at E[k], L[r].
+ *   E:     device [n] double, MeV, > 0
+ *   L:     host [nL] double, km; nL in 1..16
+ *   p:     host, one parameter point
+ *   prec:  GNA_FP64 writes double P; the mixed modes write float P
+ *   P_out: device [nL][n] of double (GNA_FP64) or float (mixed)
+ * n = 0 is valid and launches nothing.  Returns GNA_EINVAL for NULL
+ * pointers or an unknown precision, GNA_ESHAPE for n < 0 or bad nL.
+ */
+gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p,
+                          gna_precision prec, void* P_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gna_plan_create: configuration stage (paper Sec. 2, Sec. 4.2): validates
+ * the description, builds every point's Gauss-Legendre energy grid on the
+ * device (nodes E_ik, 1/E_ik and the weights (b-a)/2 w_k S(E_ik)), and
+ * allocates all scratch.  Nothing is allocated by the evaluation calls.
+ * *out receives the plan (NULL on failure).  Work is enqueued on `stream`
+ * and the call synchronises it before returning.
+ */
+gna_status gna_plan_create(gna_plan** out, const gna_plan_desc* desc, void* stream);
+
+/* gna_plan_destroy: frees everything the plan owns.  NULL is a no-op. */
+gna_status gna_plan_destroy(gna_plan* plan);
+
+/* gna_plan_error: text of the plan's last error ("" if none).  Owned by the plan. */
+const char* gna_plan_error(const gna_plan* plan);
+
+/* gna_plan_status: synchronises the stream of the plan's last call and
+ * returns the device status word (GNA_OK, GNA_ETIMEOUT, ...) or GNA_ECUDA
+ * if an asynchronous CUDA error was raised.  Clears the status word. */
+gna_status gna_plan_status(gna_plan* plan);
+
+/* gna_plan_info: sizes of the plan (host pointers; any may be NULL):
+ * total energy nodes over all points, probability evaluations per call
+ * (nodes x baselines), and device bytes owned. */
+gna_status gna_plan_info(const gna_plan* plan, int64_t* nodes, int64_t* points_per_eval, int64_t* device_bytes);
+
+/* ---------------------------------------------------------------------------
+ * gna_chain_eval: computational stage, one fused evaluation of all npts
+ * points: phase -> sin^2 -> P -> W P -> Gauss-Legendre bin sums (and the four
+ * tangents when out->grad or out->grad_eta is set) -> baseline combination
+ * -> nuisance normalisation -> chi^2 -> gradient contraction.
+ *   params: device [npts] gna_osc
+ *   eta:    device [nbins] nuisances (shared by all points) or NULL
+ *   sigma_eta: nuisance sigma; the penalty sum eta_i^2 / sigma^2 is added
+ *           when eta != NULL and sigma_eta > 0
+ *   data:   device [npts][nbins] if data_per_point else [nbins]
+ *   out:    host struct of device pointers
+ * Precision follows the plan.  Asynchronous on `stream`.
+ */
+gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                          const double* data, int data_per_point, const gna_outputs* out, void* stream);
+
+/* gna_chain_eval_host: the same evaluation from HOST buffers: copies params
+ * [npts], eta [nbins] (or NULL) and data to the plan's device staging
+ * buffers, evaluates, copies chi2 [npts], grad [npts][4] (if grad != NULL)
+ * and spectra [npts][nL][nbins] (if spectra != NULL; GNA_ESHAPE when that
+ * exceeds 2^24 values) back to the host and synchronises the stream.  Host
+ * buffers should be pinned for full copy speed. */
+gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                               const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
+                               void* stream);
+
+/* gna_chain_eval_plain: the same outputs computed by the plain FP64 chain,
+ * one kernel per transformation as in the paper (OscProb and its tangents ->
+ * weight -> bin integration -> chi^2), intermediates in device memory, CUDA's
+ * double sin/cos.  Needs a plan created with GNA_PLAN_WITH_PLAIN and uniform
+ * node counts (node_counts == NULL or all equal).  Points are processed one
+ * after another.  The reference against which the fused path is measured. */
+gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                                const double* data, int data_per_point, const gna_outputs* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gna_fit_batch: batched Levenberg-Marquardt fits of the four oscillation
+ * parameters, one per point/dataset (the paper has no fitter; its Sec. 2.1
+ * describes minimisation as the consumer of the prediction).  Each of the
+ * `iters` iterations is one fused chi^2 + gradient + J^T W J evaluation of
+ * all npts points followed by one device kernel that accepts or rejects the
+ * trial (lambda /10 or x10), solves (H + lambda diag H) delta = -g (4x4,
+ * FP64) and clamps the next trial into s2 in [1e-6, 1-1e-6], dm2 >= 1e-7.
+ *   params: device [npts] gna_osc; in: start points; out: best points
+ *   data:   device [npts][nbins]
+ *   chi2_out: device [npts] best chi^2
+ *   lambda0: initial damping (e.g. 1e-3)
+ * With use_graph != 0 one iteration is captured once into a CUDA graph and
+ * replayed `iters` times.  Asynchronous on `stream`.
+ */
+gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, int iters, double lambda0,
+                         double* chi2_out, int use_graph, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch shape, autotuning and graphs.
+ * gna_plan_autotune: times the candidate launch shapes (threads per block,
+ * nodes per thread, grid size) for this plan on `stream` with CUDA events
+ * over `reps` evaluations each (with the given arguments, gradient on) and
+ * keeps the fastest.  The choice can be read back and restored as text
+ * ("block=256 nodes=16 grid=1216") for caching between runs.
+ */
+gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point,
+                             int reps, void* stream);
+gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen);
+gna_status gna_plan_set_tuning(gna_plan* plan, const char* text);
+
+/* gna_plan_set_graph: with on != 0, gna_chain_eval captures its launches
+ * into a CUDA graph the first time it sees a given set of argument pointers
+ * and replays that graph afterwards (device contents may change between
+ * calls; pointers may not without a new capture). */
+gna_status gna_plan_set_graph(gna_plan* plan, int on);
+
+/* gna_plan_kernel_launches: kernels launched by the most recent evaluation
+ * call (graph replays count the kernels inside the graph). */
+int gna_plan_kernel_launches(const gna_plan* plan);
+
+/* gna_plan_profile: with on != 0, every evaluation outside graph capture
+ * records a pair of CUDA events on its stream around the fused node kernel
+ * (up to 8192 pairs).  gna_plan_profile_read synchronises those events and
+ * returns the summed kernel time in ms and the number of timed launches,
+ * then clears them. */
+gna_status gna_plan_profile(gna_plan* plan, int on);
+gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches);
+
+/* gna_plan_set_wait_limit: iteration limit of bounded device-side waits
+ * (for tests; 0 restores the default). */
+gna_status gna_plan_set_wait_limit(gna_plan* plan, int64_t limit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GNAOSC_H */

@@ -191,6 +191,8 @@ void or_pee_grad(const double* E_MeV, int64_t n, double L_km, const double* osc,
 /* recurrence (j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}, started from          */
 /* cos(pi (k - 1/4) / (n + 1/2)); weights w = 2 / ((1 - x^2) P_n'(x)^2) with  */
 /* P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1).  Nodes returned ascending.      */
+/* (x^2 - 1 is evaluated as (x - 1)(x + 1) to avoid cancellation at the      */
+/* outermost nodes.)                                                          */
 /* Returns 0, or -1 for n < 1.                                                */
 /* ------------------------------------------------------------------------ */
 static void legendre_eval(int n, double x, double* pn, double* pn1) {
@@ -218,16 +220,17 @@ int or_gl(int n, double* x, double* w) {
         double pn = 0, pn1 = 0, dp = 0;
         for (int it = 0; it < 100; it++) {
             legendre_eval(n, xk, &pn, &pn1);
-            dp = n * (xk * pn - pn1) / (xk * xk - 1.0);
+            dp = n * (xk * pn - pn1) / ((xk - 1.0) * (xk + 1.0));
             double dx = pn / dp;
             xk -= dx;
             if (fabs(dx) <= 1e-16 * (1.0 + fabs(xk))) break;
         }
         legendre_eval(n, xk, &pn, &pn1);
-        dp = n * (xk * pn - pn1) / (xk * xk - 1.0);
-        /* k = 1 is the largest root; store ascending */
+        dp = n * (xk * pn - pn1) / ((xk - 1.0) * (xk + 1.0));
+        /* k = 1 is the largest root; store ascending.  1 - x^2 is formed as
+         * (1 - x)(1 + x): near x = +-1 the difference is then exact. */
         x[n - k] = xk;
-        w[n - k] = 2.0 / ((1.0 - xk * xk) * dp * dp);
+        w[n - k] = 2.0 / (((1.0 - xk) * (1.0 + xk)) * dp * dp);
     }
     return 0;
 }

@@ -1,0 +1,267 @@
+"""Python binding of libgnaosc.so: argument marshalling over the C ABI.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+chain runs in the library's kernels.  There is no CPU path: if the library is
+missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+PRECISIONS = {"fp64": N.GNA_FP64, "f64phase": N.GNA_MIXED_F64PHASE, "ff": N.GNA_MIXED_FFPHASE}
+KINDS = {"pearson": N.GNA_PEARSON, "poisson": N.GNA_POISSON, 0: N.GNA_PEARSON, 1: N.GNA_POISSON}
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("the oscillation library needs a CUDA device")
+    N.lib()
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def gl_nodes(n: int, device="cuda"):
+    """n-point Gauss-Legendre nodes (ascending) and weights on [-1, 1], computed on the device."""
+    _require_cuda()
+    x = torch.empty(n, dtype=torch.float64, device=device)
+    w = torch.empty(n, dtype=torch.float64, device=device)
+    N.check(N.lib().gna_gl_nodes(int(n), _ptr(x), _ptr(w), ctypes.c_void_p(_stream())), what="gna_gl_nodes")
+    return x, w
+
+
+def oscprob(E: torch.Tensor, L: Sequence[float], theta: Sequence[float], prec: str = "fp64") -> torch.Tensor:
+    """Element-wise OscProb: P(nue_bar -> nue_bar) [nL, n] at energies E (MeV) for baselines L (km)."""
+    _require_cuda()
+    if E.dtype != torch.float64:
+        raise ValueError("E must be float64")
+    Ls = _f64(L)
+    p = N.GnaOsc(*[float(t) for t in theta])
+    out_dtype = torch.float64 if prec == "fp64" else torch.float32
+    P = torch.empty((Ls.size, E.numel()), dtype=out_dtype, device=E.device)
+    code = N.lib().gna_oscprob_ee(_ptr(E.contiguous()), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  Ls.size, ctypes.byref(p), PRECISIONS[prec], _ptr(P), ctypes.c_void_p(_stream()))
+    N.check(code, what="gna_oscprob_ee")
+    return P
+
+
+class Plan:
+    """A configured chain (paper's configuration stage): energy grids built and
+    all scratch allocated on the device; evaluations only launch kernels."""
+
+    def __init__(self, edges, L, nodes_per_bin: int = 0, npts: int = 1, node_counts=None, Lweight=None,
+                 norm: float = 1.0, e_scale: float = 1.0, prec: str = "ff", kind="pearson", max_datasets: int = 0,
+                 with_plain: bool = False, mapping: Optional[str] = None, stream=None):
+        _require_cuda()
+        self._lib = N.lib()
+        self._edges = _f64(edges)
+        self._L = _f64(np.atleast_1d(L))
+        self._Lw = None if Lweight is None else _f64(Lweight)
+        self._counts = None if node_counts is None else np.ascontiguousarray(np.asarray(node_counts, dtype=np.int32))
+        self.nbins = self._edges.size - 1
+        self.npts = int(npts)
+        self.nL = self._L.size
+        self.prec = prec
+        flags = N.GNA_PLAN_WITH_PLAIN if with_plain else 0
+        if mapping == "split":
+            flags |= N.GNA_PLAN_FORCE_SPLIT
+        elif mapping == "bins":
+            flags |= N.GNA_PLAN_FORCE_BINS
+        P = ctypes.POINTER(ctypes.c_double)
+        d = N.GnaPlanDesc()
+        d.nbins = self.nbins
+        d.edges = self._edges.ctypes.data_as(P)
+        d.nodes_per_bin = int(nodes_per_bin)
+        d.npts = self.npts
+        d.node_counts = None if self._counts is None else self._counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.nL = self.nL
+        d.L = self._L.ctypes.data_as(P)
+        d.Lweight = None if self._Lw is None else self._Lw.ctypes.data_as(P)
+        d.norm = float(norm)
+        d.e_scale = float(e_scale)
+        d.prec = PRECISIONS[prec]
+        d.kind = KINDS[kind]
+        d.max_datasets = int(max_datasets)
+        d.flags = flags
+        h = ctypes.c_void_p()
+        code = self._lib.gna_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(_stream(stream)))
+        N.check(code, what="gna_plan_create")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._scratch = {}
+
+    # ------------------------------------------------------------ basics --
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gna_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code, what):
+        N.check(code, self._h, what)
+
+    def status(self):
+        self._check(self._lib.gna_plan_status(self._h), "gna_plan_status")
+
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.gna_plan_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "info")
+        return {"nodes": a.value, "points_per_eval": b.value, "device_bytes": c.value}
+
+    @property
+    def launches(self) -> int:
+        return self._lib.gna_plan_kernel_launches(self._h)
+
+    @property
+    def tuning(self) -> str:
+        buf = ctypes.create_string_buffer(128)
+        self._check(self._lib.gna_plan_get_tuning(self._h, buf, 128), "get_tuning")
+        return buf.value.decode()
+
+    @tuning.setter
+    def tuning(self, text: str):
+        self._check(self._lib.gna_plan_set_tuning(self._h, text.encode()), "set_tuning")
+
+    def set_graph(self, on: bool):
+        self._check(self._lib.gna_plan_set_graph(self._h, int(bool(on))), "set_graph")
+
+    def profile(self, on: bool):
+        """Record CUDA events around the fused node kernel of each evaluation."""
+        self._check(self._lib.gna_plan_profile(self._h, int(bool(on))), "profile")
+
+    def profile_read(self):
+        """(summed fused-kernel ms, timed launches) since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_int()
+        self._check(self._lib.gna_plan_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)), "profile_read")
+        return ms.value, n.value
+
+    def set_wait_limit(self, limit: int):
+        self._check(self._lib.gna_plan_set_wait_limit(self._h, int(limit)), "set_wait_limit")
+
+    # ------------------------------------------------------- evaluation --
+    def params_tensor(self, theta) -> torch.Tensor:
+        t = torch.as_tensor(np.asarray(theta, dtype=np.float64).reshape(-1, 4), device=self.device)
+        if t.shape[0] != self.npts:
+            raise ValueError("expected %d parameter points" % self.npts)
+        return t.contiguous()
+
+    def _out(self, name, shape):
+        return torch.empty(shape, dtype=torch.float64, device=self.device)
+
+    def eval(self, params: torch.Tensor, data: torch.Tensor, eta: Optional[torch.Tensor] = None, sigma: float = 0.0,
+             grad: bool = True, grad_eta: bool = False, mu: bool = False, spectra: bool = False, plain: bool = False,
+             out: Optional[dict] = None, stream=None) -> dict:
+        """One evaluation of all points.  params [npts, 4] float64 CUDA; data [nbins] or [npts, nbins]."""
+        if params.dtype != torch.float64 or tuple(params.shape) != (self.npts, 4):
+            raise ValueError("params must be float64 [npts, 4]")
+        dpp = 1 if data.dim() == 2 else 0
+        if data.dtype != torch.float64 or data.shape[-1] != self.nbins or (dpp and data.shape[0] != self.npts):
+            raise ValueError("data must be float64 [nbins] or [npts, nbins]")
+        if eta is not None and (eta.dtype != torch.float64 or eta.numel() != self.nbins):
+            raise ValueError("eta must be float64 [nbins]")
+        if out is None:
+            out = {"chi2": self._out("chi2", (self.npts,))}
+            if grad:
+                out["grad"] = self._out("grad", (self.npts, 4))
+            if grad_eta:
+                out["grad_eta"] = self._out("grad_eta", (self.npts, self.nbins))
+            if mu:
+                out["mu"] = self._out("mu", (self.npts, self.nbins))
+            if spectra:
+                out["spectra"] = self._out("spectra", (self.npts, self.nL, self.nbins))
+        o = N.GnaOutputs(_ptr(out["chi2"]), _ptr(out.get("grad")), _ptr(out.get("grad_eta")), _ptr(out.get("mu")),
+                         _ptr(out.get("spectra")))
+        fn = self._lib.gna_chain_eval_plain if plain else self._lib.gna_chain_eval
+        code = fn(self._h, _ptr(params), _ptr(eta), float(sigma), _ptr(data), dpp, ctypes.byref(o),
+                  ctypes.c_void_p(_stream(stream)))
+        self._check(code, "gna_chain_eval_plain" if plain else "gna_chain_eval")
+        return out
+
+    def eval_host(self, params: np.ndarray, data: np.ndarray, eta: Optional[np.ndarray] = None, sigma: float = 0.0,
+                  grad: bool = True, chi2_out: Optional[np.ndarray] = None, grad_out: Optional[np.ndarray] = None,
+                  spectra_out: Optional[np.ndarray] = None, stream=None):
+        """Evaluation from host buffers (copies in, evaluates, copies out, synchronises)."""
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.npts, 4)
+        d = np.ascontiguousarray(data, dtype=np.float64)
+        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        dpp = 1 if d.ndim == 2 else 0
+        c = chi2_out if chi2_out is not None else np.empty(self.npts)
+        g = (grad_out if grad_out is not None else np.empty((self.npts, 4))) if grad else None
+        vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+        code = self._lib.gna_chain_eval_host(self._h, vp(p), vp(e), float(sigma), vp(d), dpp, vp(c), vp(g),
+                                             vp(spectra_out), ctypes.c_void_p(_stream(stream)))
+        self._check(code, "gna_chain_eval_host")
+        return c, g
+
+    def fit(self, params: torch.Tensor, data: torch.Tensor, iters: int = 20, lambda0: float = 1e-3,
+            graph: bool = True, chi2_out: Optional[torch.Tensor] = None, stream=None):
+        """Batched Levenberg-Marquardt fits; params [npts, 4] is overwritten with the best points."""
+        if chi2_out is None:
+            chi2_out = self._out("fit_chi2", (self.npts,))
+        code = self._lib.gna_fit_batch(self._h, _ptr(params), _ptr(data), int(iters), float(lambda0), _ptr(chi2_out),
+                                       int(bool(graph)), ctypes.c_void_p(_stream(stream)))
+        self._check(code, "gna_fit_batch")
+        return params, chi2_out
+
+    def autotune(self, params: torch.Tensor, data: torch.Tensor, reps: int = 3, stream=None) -> str:
+        dpp = 1 if data.dim() == 2 else 0
+        code = self._lib.gna_plan_autotune(self._h, _ptr(params), _ptr(data), dpp, int(reps),
+                                           ctypes.c_void_p(_stream(stream)))
+        self._check(code, "gna_plan_autotune")
+        return self.tuning
+
+
+class OscChi2(torch.autograd.Function):
+    """chi^2(theta, eta) of one plan point with its hand-written gradient.
+
+    forward runs one fused evaluation with the tangents on and keeps
+    d chi2 / d theta (and d chi2 / d eta); backward returns grad_output times
+    the kept gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, eta, plan: Plan, data, sigma: float = 0.0):
+        if plan.npts != 1:
+            raise ValueError("OscChi2 works on a single-point plan")
+        p = theta.detach().reshape(1, 4).contiguous()
+        e = None if eta is None else eta.detach().contiguous()
+        r = plan.eval(p, data, e, sigma, grad=True, grad_eta=e is not None)
+        ctx.save_for_backward(r["grad"][0].clone(), r["grad_eta"][0].clone() if e is not None else torch.zeros(0))
+        ctx.has_eta = e is not None
+        return r["chi2"][0].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        gt, ge = ctx.saved_tensors
+        return g * gt, (g * ge if ctx.has_eta else None), None, None, None
+
+
+def chi2(theta, plan: Plan, data, eta=None, sigma: float = 0.0):
+    return OscChi2.apply(theta, eta, plan, data, sigma)

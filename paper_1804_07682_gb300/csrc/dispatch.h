@@ -1,0 +1,13 @@
+// dispatch.h -- host-side selection of the fused-kernel instantiation.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gna {
+// ph: 0 = double-float phase, 1 = double phase (both FP32 + Kahan bulk), 2 = all double.
+// nl: instantiated baseline count (1, 2, 4, 8 or 16).  args points to
+// SplitArgs / BinArgs (ph 0, 1) or SplitArgs64 / BinArgs64 (ph 2).
+cudaError_t dispatch_split(int ph, int nl, bool grad, bool spec, const void* args, int grid, int block, cudaStream_t s);
+cudaError_t dispatch_bins(int ph, int nl, bool grad, bool spec, const void* args, int grid, int block, cudaStream_t s);
+// registers per thread of the split kernel (for occupancy-aware grid sizing)
+int split_regs(int ph, int nl, bool grad, bool spec);
+}  // namespace gna

@@ -1,0 +1,256 @@
+// fused.cuh -- the fused probability -> weight -> bin-integrate kernels.
+//
+// One pass over the energy nodes computes, per node, the survival
+// probability of every baseline (paper Sec. 4.1 formula, alpha = beta = e),
+// folds the baselines with their weights omega_r, multiplies by the node's
+// spectrum x Gauss-Legendre weight and accumulates the bin sum of the
+// prediction and of its four tangents with Kahan compensation.
+//
+// Per node (invE = 1/E, W = (b-a)/2 w_k S(E), We = W invE) and baseline r:
+//   D21 = c21_r invE, D32 = c32_r invE reduced mod pi (c = K dm2 L_r),
+//   (sin, cos) of both by FP32 polynomials, D31 = D21 + D32 by angle addition,
+//   U_ij += omega_r sin^2 D_ij,   V_ij += 2 omega_r K L_r sin D_ij cos D_ij.
+// Then Pc = sum_r omega_r P_r = sum omega - sum_ij A_ij U_ij, and
+//   d Pc / d s2_12 = -sum_ij dA12_ij U_ij, d Pc / d s2_13 = -sum_ij dA13_ij U_ij,
+//   d Pc / d dm2_21 = -invE (A21 V21 + A31 V31), d Pc / d dm2_32 = -invE (A31 V31 + A32 V32).
+// Accumulated values per (point, bin): [0] sum W Pc, [1..4] sum of W (or We)
+// times the bracketed tangent terms (sign applied in the epilogue), then
+// [5 + r] sum W P_r per baseline when spectra are requested.
+#pragma once
+
+#include "common.cuh"
+
+namespace gna {
+
+// Phase-evaluation policy: 0 = double-float (FF), 1 = double (F64 phase).
+template <int PH, int NL>
+struct PhaseConsts {
+    float ch21[NL], cl21[NL], ch32[NL], cl32[NL];
+    double cd21[NL], cd32[NL];
+
+    __device__ __forceinline__ void load(const PointConst* pc) {
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            if (PH == 0) {
+                ch21[r] = pc->c21h[r];
+                cl21[r] = pc->c21l[r];
+                ch32[r] = pc->c32h[r];
+                cl32[r] = pc->c32l[r];
+            } else {
+                cd21[r] = pc->c21[r];
+                cd32[r] = pc->c32[r];
+            }
+        }
+    }
+};
+
+template <int PH, int NL, bool GRAD, bool SPEC>
+struct NodeMath {
+    static constexpr int NV = 1 + (GRAD ? 4 : 0) + (SPEC ? NL : 0);
+
+    PhaseConsts<PH, NL> ph;
+    float om[NL], wkl[NL];
+    float wsum;
+    float A21, A31, A32;
+    float d12[3], d13[3];
+
+    __device__ __forceinline__ void load(const PointConst* pc, const BaseConst& bc) {
+        ph.load(pc);
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            om[r] = bc.om[r];
+            wkl[r] = bc.wkl[r];
+        }
+        wsum = bc.wsum;
+        A21 = pc->Af[0];
+        A31 = pc->Af[1];
+        A32 = pc->Af[2];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            d12[j] = pc->dA12f[j];
+            d13[j] = pc->dA13f[j];
+        }
+    }
+
+    // One energy node: g = {invE_hi, invE_lo, W, We}.
+    __device__ __forceinline__ void update(float4 g, KahanF (&acc)[NV]) const {
+        const float eh = g.x, el = g.y, W = g.z, We = g.w;
+        double ed = 0.0;
+        if (PH == 1) ed = (double)eh + (double)el;
+        float U21 = 0.f, U31 = 0.f, U32 = 0.f;
+        float V21 = 0.f, V31 = 0.f, V32 = 0.f;
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            float r21, r32;
+            if (PH == 0) {
+                r21 = reduce_pi_ff(ph.ch21[r], ph.cl21[r], eh, el);
+                r32 = reduce_pi_ff(ph.ch32[r], ph.cl32[r], eh, el);
+            } else {
+                r21 = reduce_pi_f64(ph.cd21[r], ed);
+                r32 = reduce_pi_f64(ph.cd32[r], ed);
+            }
+            float s1, c1, s2, c2;
+            sincos_poly(r21, s1, c1);
+            sincos_poly(r32, s2, c2);
+            // D31 = D21 + D32 (up to a multiple of pi, which flips a common sign
+            // of sin and cos and leaves sin^2 and sin cos unchanged)
+            float s3 = fmaf(s1, c2, c1 * s2);
+            float S21 = s1 * s1, S31 = s3 * s3, S32 = s2 * s2;
+            U21 = fmaf(om[r], S21, U21);
+            U31 = fmaf(om[r], S31, U31);
+            U32 = fmaf(om[r], S32, U32);
+            if (GRAD) {
+                float c3 = fmaf(c1, c2, -(s1 * s2));
+                V21 = fmaf(wkl[r], s1 * c1, V21);
+                V31 = fmaf(wkl[r], s3 * c3, V31);
+                V32 = fmaf(wkl[r], s2 * c2, V32);
+            }
+            if (SPEC) {
+                float Pr = fmaf(-A32, S32, fmaf(-A31, S31, fmaf(-A21, S21, 1.0f)));
+                kadd_prod(acc[1 + (GRAD ? 4 : 0) + r], W, Pr);
+            }
+        }
+        float Pc = fmaf(-A32, U32, fmaf(-A31, U31, fmaf(-A21, U21, wsum)));
+        kadd_prod(acc[0], W, Pc);
+        if (GRAD) {
+            float g12 = fmaf(d12[2], U32, fmaf(d12[1], U31, d12[0] * U21));
+            float g13 = fmaf(d13[2], U32, fmaf(d13[1], U31, d13[0] * U21));
+            float g21 = fmaf(A31, V31, A21 * V21);
+            float g32 = fmaf(A32, V32, A31 * V31);
+            kadd_prod(acc[1], W, g12);
+            kadd_prod(acc[2], W, g13);
+            kadd_prod(acc[3], We, g21);
+            kadd_prod(acc[4], We, g32);
+        }
+    }
+};
+
+__host__ __device__ constexpr int pow2ceil(int v) { return v <= 1 ? 1 : v <= 2 ? 2 : v <= 4 ? 4 : v <= 8 ? 8 : v <= 16 ? 16 : 32; }
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// ---------------------------------------------------------------------------
+// Split mapping: a CTA tile is (point p, bin i, node chunk c); the threads
+// stride over the chunk's nodes (bin-major grid: node k of bin i at i*n + k,
+// coalesced 16-byte loads), then the CTA reduces its Kahan sums with a
+// transposed warp-shuffle reduction and shared memory.  Persistent grid:
+// CTAs loop over tiles.
+struct SplitArgs {
+    const float4* grid;
+    int nbins, n, chunk, nchunks, npts;
+    const PointConst* pcs;
+    BaseConst bc;
+    float2* part;  // [npts][nbins][nchunks][NV]
+};
+
+template <int PH, int NL, bool GRAD, bool SPEC>
+__global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
+    using M = NodeMath<PH, NL, GRAD, SPEC>;
+    constexpr int NV = M::NV;
+    constexpr int NVP = pow2ceil(NV);
+    constexpr int SH = 5 - ilog2(NVP);
+    __shared__ float2 red[8][NVP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
+    int last_p = -1;
+    M m;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int c = (int)(tile % a.nchunks);
+        const int64_t t2 = tile / a.nchunks;
+        const int i = (int)(t2 % a.nbins);
+        const int p = (int)(t2 / a.nbins);
+        if (p != last_p) {
+            m.load(a.pcs + p, a.bc);
+            last_p = p;
+        }
+        KahanF acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) kzero(acc[v]);
+        const int k0 = c * a.chunk;
+        const int k1 = min(a.n, k0 + a.chunk);
+        const float4* g = a.grid + (int64_t)i * a.n;
+        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) m.update(__ldg(g + k), acc);
+        float2 v[NVP];
+#pragma unroll
+        for (int j = 0; j < NVP; j++) v[j] = (j < NV) ? kahan_to_ff(acc[j < NV ? j : 0]) : make_float2(0.f, 0.f);
+        warp_transpose_reduce<NVP>(v, lane);
+        if ((lane & ((1 << SH) - 1)) == 0) red[warp][lane >> SH] = v[0];
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            float2 s = red[0][threadIdx.x];
+            for (int w = 1; w < nwarps; w++) s = ff_add(s, red[w][threadIdx.x]);
+            a.part[(((int64_t)p * a.nbins + i) * a.nchunks + c) * NV + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bin mapping: a warp task is (point p, group b of 32 consecutive bins); lane
+// l owns bin 32 b + l and walks all its nodes (grid layout [group][k][lane],
+// so each warp load is 512 contiguous bytes).  No cross-thread reduction.
+// Warps take tasks from a global counter; tasks are ordered by decreasing
+// node count so that uneven grids balance.
+struct BinArgs {
+    const float4* grid;
+    const int64_t* goff;  // [ngrids] float4 offset of each grid
+    const int* gn;        // [ngrids] Gauss-Legendre order of each grid
+    int shared_grid;      // 1: every point uses grid 0
+    const int* tasks;     // [ntasks] p * ngroups + b, in execution order
+    int ntasks, ngroups, nbins;
+    const PointConst* pcs;
+    BaseConst bc;
+    float2* part;  // [npts][nbins][NV]
+    int* counter;  // zeroed before the launch
+};
+
+template <int PH, int NL, bool GRAD, bool SPEC>
+__global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
+    using M = NodeMath<PH, NL, GRAD, SPEC>;
+    constexpr int NV = M::NV;
+    const int lane = threadIdx.x & 31;
+    int last_p = -1;
+    M m;
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.ntasks) break;
+        const int task = a.tasks[t];
+        const int p = task / a.ngroups;
+        const int b = task - p * a.ngroups;
+        const int gi = a.shared_grid ? 0 : p;
+        const int n = a.gn[gi];
+        if (p != last_p) {
+            m.load(a.pcs + p, a.bc);
+            last_p = p;
+        }
+        KahanF acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) kzero(acc[v]);
+        const float4* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
+        for (int k = 0; k < n; k++) m.update(__ldg(g + (int64_t)k * 32), acc);
+        const int i = b * 32 + lane;
+        if (i < a.nbins) {
+            float2* o = a.part + ((int64_t)p * a.nbins + i) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; v++) o[v] = kahan_to_ff(acc[v]);
+        }
+    }
+}
+
+template <int PH, int NL, bool GRAD, bool SPEC>
+cudaError_t launch_split(const SplitArgs& a, int grid, int block, cudaStream_t s) {
+    k_fused_split<PH, NL, GRAD, SPEC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PH, int NL, bool GRAD, bool SPEC>
+cudaError_t launch_bins(const BinArgs& a, int grid, int block, cudaStream_t s) {
+    k_fused_bins<PH, NL, GRAD, SPEC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Number of values per (point, bin) for the given flags.
+__host__ __device__ inline int fused_nv(int nl, bool grad, bool spec) { return 1 + (grad ? 4 : 0) + (spec ? nl : 0); }
+
+}  // namespace gna

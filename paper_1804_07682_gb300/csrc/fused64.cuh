@@ -1,0 +1,179 @@
+// fused64.cuh -- the fused chain with every step in double precision
+// (GNA_FP64).  Same mappings as fused.cuh; the phase is reduced modulo pi in
+// double and sin/cos are CUDA's double sincos on the reduced argument.
+#pragma once
+
+#include "common.cuh"
+#include "fused.cuh"
+
+namespace gna {
+
+template <int NL, bool GRAD, bool SPEC>
+struct NodeMath64 {
+    static constexpr int NV = 1 + (GRAD ? 4 : 0) + (SPEC ? NL : 0);
+    double c21[NL], c32[NL], om[NL], kl2[NL];
+    double omsum, A21, A31, A32, d12[3], d13[3];
+
+    __device__ __forceinline__ void load(const PointConst* pc, const BaseConst& bc) {
+        omsum = 0.0;
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            c21[r] = pc->c21[r];
+            c32[r] = pc->c32[r];
+            om[r] = bc.omd[r];
+            kl2[r] = 2.0 * bc.omd[r] * bc.kld[r];
+            omsum += bc.omd[r];
+        }
+        A21 = pc->A[0];
+        A31 = pc->A[1];
+        A32 = pc->A[2];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            d12[j] = pc->dA12[j];
+            d13[j] = pc->dA13[j];
+        }
+    }
+
+    // g = {invE, W}
+    __device__ __forceinline__ void update(double2 g, double (&acc)[NV]) const {
+        const double e = g.x, W = g.y;
+        double U21 = 0, U31 = 0, U32 = 0, V21 = 0, V31 = 0, V32 = 0;
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            double s1, c1, s2, c2;
+            sincos(reduce_pi_d(c21[r] * e), &s1, &c1);
+            sincos(reduce_pi_d(c32[r] * e), &s2, &c2);
+            double s3 = s1 * c2 + c1 * s2;
+            double S21 = s1 * s1, S31 = s3 * s3, S32 = s2 * s2;
+            U21 += om[r] * S21;
+            U31 += om[r] * S31;
+            U32 += om[r] * S32;
+            if (GRAD) {
+                double c3 = c1 * c2 - s1 * s2;
+                V21 += kl2[r] * s1 * c1;
+                V31 += kl2[r] * s3 * c3;
+                V32 += kl2[r] * s2 * c2;
+            }
+            if (SPEC) acc[1 + (GRAD ? 4 : 0) + r] += W * (1.0 - A21 * S21 - A31 * S31 - A32 * S32);
+        }
+        acc[0] += W * (omsum - A21 * U21 - A31 * U31 - A32 * U32);
+        if (GRAD) {
+            acc[1] += W * (d12[0] * U21 + d12[1] * U31 + d12[2] * U32);
+            acc[2] += W * (d13[0] * U21 + d13[1] * U31 + d13[2] * U32);
+            acc[3] += W * e * (A21 * V21 + A31 * V31);
+            acc[4] += W * e * (A31 * V31 + A32 * V32);
+        }
+    }
+};
+
+struct SplitArgs64 {
+    const double2* grid;
+    int nbins, n, chunk, nchunks, npts;
+    const PointConst* pcs;
+    BaseConst bc;
+    double* part;  // [npts][nbins][nchunks][NV]
+};
+
+template <int NL, bool GRAD, bool SPEC>
+__global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
+    using M = NodeMath64<NL, GRAD, SPEC>;
+    constexpr int NV = M::NV;
+    __shared__ double red[8][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
+    int last_p = -1;
+    M m;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int c = (int)(tile % a.nchunks);
+        const int64_t t2 = tile / a.nchunks;
+        const int i = (int)(t2 % a.nbins);
+        const int p = (int)(t2 / a.nbins);
+        if (p != last_p) {
+            m.load(a.pcs + p, a.bc);
+            last_p = p;
+        }
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) acc[v] = 0.0;
+        const int k0 = c * a.chunk;
+        const int k1 = min(a.n, k0 + a.chunk);
+        const double2* g = a.grid + (int64_t)i * a.n;
+        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) m.update(g[k], acc);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            double x = acc[v];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) red[warp][v] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double s = red[0][threadIdx.x];
+            for (int w = 1; w < nwarps; w++) s += red[w][threadIdx.x];
+            a.part[(((int64_t)p * a.nbins + i) * a.nchunks + c) * NV + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+struct BinArgs64 {
+    const double2* grid;
+    const int64_t* goff;
+    const int* gn;
+    int shared_grid;
+    const int* tasks;
+    int ntasks, ngroups, nbins;
+    const PointConst* pcs;
+    BaseConst bc;
+    double* part;  // [npts][nbins][NV]
+    int* counter;
+};
+
+template <int NL, bool GRAD, bool SPEC>
+__global__ void __launch_bounds__(256) k_fused64_bins(BinArgs64 a) {
+    using M = NodeMath64<NL, GRAD, SPEC>;
+    constexpr int NV = M::NV;
+    const int lane = threadIdx.x & 31;
+    int last_p = -1;
+    M m;
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.ntasks) break;
+        const int task = a.tasks[t];
+        const int p = task / a.ngroups;
+        const int b = task - p * a.ngroups;
+        const int gi = a.shared_grid ? 0 : p;
+        const int n = a.gn[gi];
+        if (p != last_p) {
+            m.load(a.pcs + p, a.bc);
+            last_p = p;
+        }
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) acc[v] = 0.0;
+        const double2* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
+        for (int k = 0; k < n; k++) m.update(g[(int64_t)k * 32], acc);
+        const int i = b * 32 + lane;
+        if (i < a.nbins) {
+            double* o = a.part + ((int64_t)p * a.nbins + i) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; v++) o[v] = acc[v];
+        }
+    }
+}
+
+template <int NL, bool GRAD, bool SPEC>
+cudaError_t launch_split64(const SplitArgs64& a, int grid, int block, cudaStream_t s) {
+    k_fused64_split<NL, GRAD, SPEC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NL, bool GRAD, bool SPEC>
+cudaError_t launch_bins64(const BinArgs64& a, int grid, int block, cudaStream_t s) {
+    k_fused64_bins<NL, GRAD, SPEC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gna

@@ -1,0 +1,888 @@
+// gnaosc.cu -- the C ABI: plans (configuration stage), evaluations
+// (computational stage), the plain FP64 chain, batched fits, autotuning and
+// CUDA-graph replay.  Paper Sec. 2 (transformations, configuration vs
+// computational stage) and Sec. 4.2 (all memory preallocated at configuration,
+// inputs are views, two host/device transfers per sub-chain, GPU status
+// readable on the host).
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dispatch.h"
+#include "fused.cuh"
+#include "fused64.cuh"
+#include "gnaosc.h"
+#include "misc.h"
+
+using namespace gna;
+
+namespace gna {
+cudaError_t dispatch_split_ph0(int, bool, bool, const void*, int, int, cudaStream_t);
+cudaError_t dispatch_bins_ph0(int, bool, bool, const void*, int, int, cudaStream_t);
+cudaError_t dispatch_split_ph1(int, bool, bool, const void*, int, int, cudaStream_t);
+cudaError_t dispatch_bins_ph1(int, bool, bool, const void*, int, int, cudaStream_t);
+cudaError_t dispatch_split_ph2(int, bool, bool, const void*, int, int, cudaStream_t);
+cudaError_t dispatch_bins_ph2(int, bool, bool, const void*, int, int, cudaStream_t);
+int split_regs_ph0(int, bool, bool);
+int split_regs_ph1(int, bool, bool);
+int split_regs_ph2(int, bool, bool);
+
+cudaError_t dispatch_split(int ph, int nl, bool grad, bool spec, const void* args, int grid, int block, cudaStream_t s) {
+    if (ph == 0) return dispatch_split_ph0(nl, grad, spec, args, grid, block, s);
+    if (ph == 1) return dispatch_split_ph1(nl, grad, spec, args, grid, block, s);
+    return dispatch_split_ph2(nl, grad, spec, args, grid, block, s);
+}
+cudaError_t dispatch_bins(int ph, int nl, bool grad, bool spec, const void* args, int grid, int block, cudaStream_t s) {
+    if (ph == 0) return dispatch_bins_ph0(nl, grad, spec, args, grid, block, s);
+    if (ph == 1) return dispatch_bins_ph1(nl, grad, spec, args, grid, block, s);
+    return dispatch_bins_ph2(nl, grad, spec, args, grid, block, s);
+}
+int split_regs(int ph, int nl, bool grad, bool spec) {
+    if (ph == 0) return split_regs_ph0(nl, grad, spec);
+    if (ph == 1) return split_regs_ph1(nl, grad, spec);
+    return split_regs_ph2(nl, grad, spec);
+}
+}  // namespace gna
+
+namespace {
+
+enum { MAP_SPLIT = 0, MAP_BINS = 1 };
+const int kDefaultBlock = 256;
+const int kDefaultNodesPerThread = 16;
+
+int inst_nl(int nl, int ph) {
+    if (ph == 0) {
+        if (nl <= 1) return 1;
+        if (nl <= 2) return 2;
+        if (nl <= 4) return 4;
+        if (nl <= 8) return 8;
+        return 16;
+    }
+    if (nl <= 1) return 1;
+    if (nl <= 8) return 8;
+    return 16;
+}
+
+struct GraphKey {
+    std::vector<uintptr_t> v;
+    bool operator==(const GraphKey& o) const { return v == o.v; }
+};
+
+}  // namespace
+
+struct gna_plan {
+    // configuration
+    int nbins = 0, npts = 0, nL = 0, nl_inst = 0, ph = 0;
+    std::vector<double> edges, L, omega;
+    std::vector<int> counts;
+    bool uniform = true;
+    int n_uniform = 0;
+    double norm = 1.0, e_scale = 1.0;
+    int prec = GNA_MIXED_FFPHASE, kind = GNA_PEARSON, flags = 0, max_datasets = 0;
+    int mapping = MAP_SPLIT;
+    int sm_count = 0;
+    // grids
+    float4* grid_ff = nullptr;
+    double2* grid64 = nullptr;
+    double2* plain64 = nullptr;
+    int64_t grid_len = 0, total_nodes = 0;
+    int64_t* d_goff = nullptr;
+    int* d_gn = nullptr;
+    int ngrids = 0, ngroups = 0;
+    int* d_tasks = nullptr;
+    int ntasks = 0;
+    int* d_counter = nullptr;
+    double* d_edges = nullptr;
+    // constants
+    BaseConst bc{};
+    PointConst* d_pc = nullptr;
+    // scratch
+    void* d_part = nullptr;
+    size_t part_cap = 0;  // elements of 8 bytes
+    double* d_binvals = nullptr;
+    double* d_H = nullptr;
+    double* d_chi2_tmp = nullptr;
+    double* d_grad_tmp = nullptr;
+    // staging for host-buffer evaluations
+    gna_osc* d_params_stage = nullptr;
+    double* d_data_stage = nullptr;
+    double* d_eta_stage = nullptr;
+    double* d_chi2_stage = nullptr;
+    double* d_grad_stage = nullptr;
+    // plain chain scratch
+    double* d_plainP = nullptr;
+    double* d_plainD = nullptr;
+    double* d_plainMu = nullptr;
+    double* d_plainDmu = nullptr;
+    // fitter
+    LMState* d_lm = nullptr;
+    // launch shape
+    int block = kDefaultBlock, npt = kDefaultNodesPerThread, grid_mult = 0;
+    // graphs
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    int graph_launches = 0;
+    // bookkeeping
+    std::string err;
+    cudaStream_t last_stream = nullptr;
+    int last_launches = 0;
+    int64_t dev_bytes = 0;
+    int* d_status = nullptr;
+    int64_t wait_limit = 0;
+    std::vector<void*> allocs;
+    // kernel timing
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_ev;  // pairs
+    int prof_n = 0;
+    double* d_spec_stage = nullptr;
+};
+
+namespace {
+
+gna_status fail(gna_plan* p, gna_status s, const char* fmt, ...) {
+    if (p) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        p->err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                                           \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) return fail(plan, GNA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+template <typename T>
+gna_status dalloc(gna_plan* plan, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) return GNA_OK;
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(plan, GNA_ENOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    plan->allocs.push_back(v);
+    plan->dev_bytes += (int64_t)(count * sizeof(T));
+    *ptr = static_cast<T*>(v);
+    return GNA_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        gna_status s_ = (x);            \
+        if (s_ != GNA_OK) return s_;    \
+    } while (0)
+
+int nchunks_of(const gna_plan* p) {
+    if (p->mapping != MAP_SPLIT) return 1;
+    const int chunk = p->block * p->npt;
+    return (p->n_uniform + chunk - 1) / chunk;
+}
+
+int value_count(const gna_plan* p, bool grad, bool spec) { return fused_nv(p->nl_inst, grad, spec); }
+
+// Persistent grid size for the current launch shape.
+int grid_size(const gna_plan* p, bool grad, bool spec, int64_t work_items) {
+    int per_sm = 2;
+    if (p->mapping == MAP_SPLIT) {
+        int regs = split_regs(p->ph, p->nl_inst, grad, spec);
+        if (regs > 0) {
+            int by_regs = 65536 / (std::max(regs, 32) * p->block);
+            int by_threads = 2048 / p->block;
+            per_sm = std::max(1, std::min(by_regs, by_threads));
+        }
+    } else {
+        per_sm = std::max(1, 1024 / p->block);
+    }
+    if (p->grid_mult > 0) per_sm = p->grid_mult;
+    int64_t g = (int64_t)p->sm_count * per_sm;
+    if (p->mapping == MAP_SPLIT) g = std::min<int64_t>(g, work_items);
+    else g = std::min<int64_t>(g, (work_items * 32 + p->block - 1) / p->block);
+    return (int)std::max<int64_t>(1, g);
+}
+
+struct EvalReq {
+    const gna_osc* params;
+    const double* eta;
+    double sigma;
+    const double* data;
+    int dpp;
+    double* chi2;
+    double* grad;      // [npts][4] or NULL
+    double* grad_eta;  // [npts][nbins] or NULL
+    double* mu;
+    double* spectra;
+    double* H;  // [npts][10] or NULL (fitter)
+};
+
+// Enqueue one fused evaluation; counts kernel launches into *launches.
+gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* launches) {
+    const bool grad = q.grad || q.grad_eta || q.H;
+    const bool spec = q.spectra != nullptr;
+    int nl = 0;
+    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s));
+    nl++;
+    const int NV = value_count(plan, grad, spec);
+    const int nchunks = nchunks_of(plan);
+    if ((size_t)plan->npts * plan->nbins * nchunks * NV > plan->part_cap)
+        return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
+                    (long long)plan->npts * plan->nbins * nchunks * NV, plan->part_cap);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
+    if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
+    if (plan->mapping == MAP_SPLIT) {
+        const int64_t tiles = (int64_t)plan->npts * plan->nbins * nchunks;
+        const int g = grid_size(plan, grad, spec, tiles);
+        if (plan->ph < 2) {
+            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
+                        plan->d_pc, plan->bc, (float2*)plan->d_part};
+            CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        } else {
+            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
+                          plan->d_pc, plan->bc, (double*)plan->d_part};
+            CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        }
+        nl++;
+    } else {
+        CU(cudaMemsetAsync(plan->d_counter, 0, sizeof(int), s));
+        const int g = grid_size(plan, grad, spec, plan->ntasks);
+        if (plan->ph < 2) {
+            BinArgs a{plan->grid_ff, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+                      plan->ngroups, plan->nbins, plan->d_pc, plan->bc, (float2*)plan->d_part, plan->d_counter};
+            CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        } else {
+            BinArgs64 a{plan->grid64, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+                        plan->ngroups, plan->nbins, plan->d_pc, plan->bc, (double*)plan->d_part, plan->d_counter};
+            CU(dispatch_bins(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        }
+        nl++;
+    }
+    if (timed) {
+        CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n + 1], s));
+        plan->prof_n++;
+    }
+    EpiArgs ea{};
+    ea.part = plan->d_part;
+    ea.is64 = plan->ph == 2;
+    ea.nchunks = nchunks;
+    ea.NV = NV;
+    ea.has_grad = grad;
+    ea.nspec = spec ? plan->nl_inst : 0;
+    ea.nL_out = plan->nL;
+    ea.npts = plan->npts;
+    ea.nbins = plan->nbins;
+    ea.norm = plan->norm;
+    ea.kind = plan->kind;
+    ea.eta = q.eta;
+    ea.sigma = q.sigma;
+    ea.data = q.data;
+    ea.data_per_point = q.dpp;
+    ea.mu_out = q.mu;
+    ea.spectra_out = q.spectra;
+    ea.grad_eta_out = q.grad_eta;
+    ea.binvals = plan->d_binvals;
+    ea.NBV = q.H ? 15 : (grad ? 5 : 1);
+    CU(launch_epilogue(ea, q.chi2, q.grad, q.H, s));
+    nl += 2;
+    *launches = nl;
+    return GNA_OK;
+}
+
+gna_status check_eval_args(gna_plan* plan, const gna_osc* params, const double* data, const gna_outputs* out, int dpp) {
+    if (!plan) return GNA_EINVAL;
+    if (!params || !data || !out || !out->chi2) return fail(plan, GNA_EINVAL, "params, data, out and out->chi2 are required");
+    if (dpp && plan->max_datasets < plan->npts)
+        return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
+    return GNA_OK;
+}
+
+void destroy_profile(gna_plan* p) {
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    p->prof_ev.clear();
+    p->prof_n = 0;
+    p->profile = false;
+}
+
+void destroy_graph(gna_plan* p) {
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    p->gkey.v.clear();
+}
+
+}  // namespace
+
+// ============================================================ C ABI ======
+extern "C" {
+
+const char* gna_strerror(gna_status s) {
+    switch (s) {
+        case GNA_OK: return "ok";
+        case GNA_EINVAL: return "invalid argument";
+        case GNA_ESHAPE: return "inconsistent or out-of-range size";
+        case GNA_ENOMEM: return "allocation failed";
+        case GNA_ECUDA: return "CUDA runtime error";
+        case GNA_ETIMEOUT: return "bounded device wait timed out";
+        case GNA_ESTATE: return "call not valid in the current state";
+    }
+    return "unknown status";
+}
+
+gna_status gna_gl_nodes(int n, double* x, double* w, void* stream) {
+    if (!x || !w) return GNA_EINVAL;
+    if (n < 1 || n > GNA_MAX_ORDER) return GNA_ESHAPE;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, 2 * sizeof(double) * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return GNA_ENOMEM;
+    }
+    cudaError_t e = launch_gl(n, x, w, tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
+}
+
+gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p, gna_precision prec,
+                          void* P_out, void* stream) {
+    if (n < 0 || nL < 1 || nL > GNA_NLMAX) return GNA_ESHAPE;
+    if (!L || !p) return GNA_EINVAL;
+    if (prec != GNA_FP64 && prec != GNA_MIXED_F64PHASE && prec != GNA_MIXED_FFPHASE) return GNA_EINVAL;
+    if (n == 0) return GNA_OK;
+    if (!E || !P_out) return GNA_EINVAL;
+    OscConst oc{};
+    oc.nL = nL;
+    const double s12 = p->s2_12, s13 = p->s2_13;
+    oc.A[0] = 4.0 * s12 * (1 - s12) * (1 - s13) * (1 - s13);
+    oc.A[1] = 4.0 * (1 - s12) * (1 - s13) * s13;
+    oc.A[2] = 4.0 * s12 * (1 - s13) * s13;
+    for (int j = 0; j < 3; j++) oc.Af[j] = (float)oc.A[j];
+    oc.one_minus_A21f = (float)(1.0 - oc.A[0]);
+    for (int r = 0; r < nL; r++) {
+        if (!(L[r] >= 0.0)) return GNA_EINVAL;
+        const double kl = GNA_K_PHASE * L[r];
+        oc.c21[r] = p->dm2_21 * kl;
+        oc.c32[r] = p->dm2_32 * kl;
+        split_ff(oc.c21[r], oc.c21h[r], oc.c21l[r]);
+        split_ff(oc.c32[r], oc.c32h[r], oc.c32l[r]);
+        split_ff(oc.c21[r] + oc.c32[r], oc.c31h[r], oc.c31l[r]);
+    }
+    cudaError_t e = launch_oscprob(E, n, oc, prec, P_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
+}
+
+gna_status gna_plan_destroy(gna_plan* plan) {
+    if (!plan) return GNA_OK;
+    destroy_graph(plan);
+    destroy_profile(plan);
+    for (void* v : plan->allocs) cudaFree(v);
+    delete plan;
+    return GNA_OK;
+}
+
+const char* gna_plan_error(const gna_plan* plan) { return plan ? plan->err.c_str() : "no plan"; }
+
+gna_status gna_plan_info(const gna_plan* plan, int64_t* nodes, int64_t* points, int64_t* bytes) {
+    if (!plan) return GNA_EINVAL;
+    if (nodes) *nodes = plan->total_nodes;
+    if (points) *points = plan->total_nodes * plan->nL * (plan->uniform ? plan->npts : 1);
+    if (bytes) *bytes = plan->dev_bytes;
+    return GNA_OK;
+}
+
+static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_t s) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&plan->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    plan->nbins = d->nbins;
+    plan->npts = d->npts;
+    plan->nL = d->nL;
+    plan->norm = d->norm;
+    plan->e_scale = d->e_scale > 0 ? d->e_scale : 1.0;
+    plan->prec = d->prec;
+    plan->kind = d->kind;
+    plan->flags = d->flags;
+    plan->max_datasets = std::max(d->max_datasets, d->npts);
+    plan->ph = (d->prec == GNA_MIXED_FFPHASE) ? 0 : (d->prec == GNA_MIXED_F64PHASE) ? 1 : 2;
+    plan->nl_inst = inst_nl(d->nL, plan->ph);
+    plan->edges.assign(d->edges, d->edges + d->nbins + 1);
+    plan->L.assign(d->L, d->L + d->nL);
+    // baseline weights
+    plan->omega.resize(d->nL);
+    double wsum = 0.0;
+    for (int r = 0; r < d->nL; r++) {
+        plan->omega[r] = d->Lweight ? d->Lweight[r] : 1.0 / (d->L[r] * d->L[r]);
+        wsum += plan->omega[r];
+    }
+    for (int r = 0; r < d->nL; r++) plan->omega[r] /= wsum;
+    // node counts
+    plan->counts.resize(d->npts);
+    for (int p = 0; p < d->npts; p++) plan->counts[p] = d->node_counts ? d->node_counts[p] : d->nodes_per_bin;
+    plan->uniform = true;
+    for (int p = 1; p < d->npts; p++)
+        if (plan->counts[p] != plan->counts[0]) plan->uniform = false;
+    plan->n_uniform = plan->counts[0];
+    // base constants
+    BaseConst& bc = plan->bc;
+    memset(&bc, 0, sizeof(bc));
+    bc.nL = d->nL;
+    double fsum = 0.0;
+    for (int r = 0; r < d->nL; r++) {
+        bc.omd[r] = plan->omega[r];
+        bc.kld[r] = GNA_K_PHASE * d->L[r];
+        bc.om[r] = (float)plan->omega[r];
+        bc.wkl[r] = (float)(2.0 * plan->omega[r] * bc.kld[r]);
+        fsum += (double)bc.om[r];
+    }
+    bc.wsum = (float)fsum;
+    // mapping
+    const int ngroups = (d->nbins + 31) / 32;
+    plan->ngroups = ngroups;
+    if (d->flags & 2) plan->mapping = MAP_SPLIT;
+    else if (d->flags & 4) plan->mapping = MAP_BINS;
+    else if (plan->uniform && (plan->n_uniform >= 1024 || (int64_t)d->npts * ngroups < 16LL * plan->sm_count))
+        plan->mapping = MAP_SPLIT;
+    else plan->mapping = MAP_BINS;
+    if (plan->mapping == MAP_SPLIT && !plan->uniform)
+        return fail(plan, GNA_EINVAL, "the split mapping needs equal node counts for all points");
+    const bool shared = plan->uniform;
+    plan->ngrids = shared ? 1 : d->npts;
+    const int nbins_pad = (plan->mapping == MAP_BINS) ? ngroups * 32 : d->nbins;
+    // grid offsets
+    std::vector<int64_t> goff(plan->ngrids);
+    std::vector<int> gn(plan->ngrids);
+    int64_t off = 0;
+    for (int g = 0; g < plan->ngrids; g++) {
+        goff[g] = off;
+        gn[g] = plan->counts[g];
+        off += (int64_t)nbins_pad * gn[g];
+    }
+    plan->grid_len = off;
+    plan->total_nodes = 0;
+    for (int g = 0; g < plan->ngrids; g++) plan->total_nodes += (int64_t)d->nbins * gn[g];
+    const bool want64 = plan->ph == 2;
+    const bool want_plain = (d->flags & GNA_PLAN_WITH_PLAIN) != 0;
+    if (want_plain && !plan->uniform) return fail(plan, GNA_EINVAL, "the plain chain needs equal node counts");
+    TRY(dalloc(plan, &plan->d_edges, d->nbins + 1));
+    CU(cudaMemcpyAsync(plan->d_edges, d->edges, sizeof(double) * (d->nbins + 1), cudaMemcpyHostToDevice, s));
+    if (plan->ph < 2) TRY(dalloc(plan, &plan->grid_ff, plan->grid_len));
+    if (want64) TRY(dalloc(plan, &plan->grid64, plan->grid_len));
+    const bool plain_alias = want_plain && want64 && plan->mapping == MAP_SPLIT;
+    if (want_plain && !plain_alias) TRY(dalloc(plan, &plan->plain64, (size_t)d->nbins * plan->n_uniform));
+    TRY(dalloc(plan, &plan->d_goff, plan->ngrids));
+    TRY(dalloc(plan, &plan->d_gn, plan->ngrids));
+    CU(cudaMemcpyAsync(plan->d_goff, goff.data(), sizeof(int64_t) * plan->ngrids, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(plan->d_gn, gn.data(), sizeof(int) * plan->ngrids, cudaMemcpyHostToDevice, s));
+    // Gauss-Legendre rules per distinct order
+    std::vector<int> orders(gn.begin(), gn.end());
+    std::sort(orders.begin(), orders.end());
+    orders.erase(std::unique(orders.begin(), orders.end()), orders.end());
+    int64_t gl_total = 0;
+    for (int n : orders) gl_total += n;
+    double *glx = nullptr, *glw = nullptr, *tmp = nullptr;
+    TRY(dalloc(plan, &glx, gl_total));
+    TRY(dalloc(plan, &glw, gl_total));
+    TRY(dalloc(plan, &tmp, 2 * (size_t)orders.back()));
+    std::map<int, int64_t> gl_off;
+    int64_t go = 0;
+    for (int n : orders) {
+        gl_off[n] = go;
+        CU(launch_gl(n, glx + go, glw + go, tmp, s));
+        go += n;
+    }
+    // energy grids
+    const int layout = (plan->mapping == MAP_BINS) ? 1 : 0;
+    for (int g = 0; g < plan->ngrids; g++) {
+        const int n = gn[g];
+        CU(launch_build_grid(d->nbins, nbins_pad, plan->d_edges, n, glx + gl_off[n], glw + gl_off[n], plan->e_scale,
+                             layout, plan->grid_ff ? plan->grid_ff + goff[g] : nullptr,
+                             plan->grid64 ? plan->grid64 + goff[g] : nullptr, (g == 0) ? plan->plain64 : nullptr, s));
+    }
+    if (plain_alias) plan->plain64 = plan->grid64;
+    // task list (bins mapping): (point, group) ordered by decreasing node count
+    if (plan->mapping == MAP_BINS) {
+        if ((int64_t)d->npts * ngroups >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many bin groups");
+        std::vector<int> order(d->npts);
+        for (int p = 0; p < d->npts; p++) order[p] = p;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return plan->counts[a] > plan->counts[b]; });
+        std::vector<int> tasks;
+        tasks.reserve((size_t)d->npts * ngroups);
+        for (int p : order)
+            for (int b = 0; b < ngroups; b++) tasks.push_back(p * ngroups + b);
+        plan->ntasks = (int)tasks.size();
+        TRY(dalloc(plan, &plan->d_tasks, tasks.size()));
+        CU(cudaMemcpyAsync(plan->d_tasks, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, s));
+        TRY(dalloc(plan, &plan->d_counter, 1));
+    }
+    // scratch
+    TRY(dalloc(plan, &plan->d_pc, d->npts));
+    const int nv_max = fused_nv(plan->nl_inst, true, true);
+    int max_chunks = 1;
+    if (plan->mapping == MAP_SPLIT) max_chunks = (plan->n_uniform + 64 * 4 - 1) / (64 * 4);  // smallest tile: 64 x 4
+    plan->part_cap = (size_t)d->npts * d->nbins * max_chunks * nv_max;
+    TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
+    TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
+    TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
+    TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
+    TRY(dalloc(plan, &plan->d_grad_tmp, (size_t)d->npts * 4));
+    TRY(dalloc(plan, &plan->d_params_stage, d->npts));
+    TRY(dalloc(plan, &plan->d_data_stage, (size_t)plan->max_datasets * d->nbins));
+    TRY(dalloc(plan, &plan->d_eta_stage, d->nbins));
+    TRY(dalloc(plan, &plan->d_chi2_stage, d->npts));
+    TRY(dalloc(plan, &plan->d_grad_stage, (size_t)d->npts * 4));
+    TRY(dalloc(plan, &plan->d_lm, d->npts));
+    if ((int64_t)d->npts * d->nL * d->nbins <= (1LL << 24))
+        TRY(dalloc(plan, &plan->d_spec_stage, (size_t)d->npts * d->nL * d->nbins));
+    TRY(dalloc(plan, &plan->d_status, 1));
+    CU(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
+    if (want_plain) {
+        const size_t nn = (size_t)d->nbins * plan->n_uniform;
+        TRY(dalloc(plan, &plan->d_plainP, nn * d->nL));
+        TRY(dalloc(plan, &plan->d_plainD, 4 * nn * d->nL));
+        TRY(dalloc(plan, &plan->d_plainMu, (size_t)d->nL * d->nbins));
+        TRY(dalloc(plan, &plan->d_plainDmu, 4 * (size_t)d->nL * d->nbins));
+    }
+    CU(cudaStreamSynchronize(s));
+    CU(cudaGetLastError());
+    plan->last_stream = s;
+    return GNA_OK;
+}
+
+gna_status gna_plan_create(gna_plan** out, const gna_plan_desc* d, void* stream) {
+    if (!out) return GNA_EINVAL;
+    *out = nullptr;
+    if (!d || !d->edges || !d->L) return GNA_EINVAL;
+    if (d->nbins < 1 || d->npts < 1 || d->nL < 1 || d->nL > GNA_NLMAX) return GNA_ESHAPE;
+    if (d->prec != GNA_FP64 && d->prec != GNA_MIXED_F64PHASE && d->prec != GNA_MIXED_FFPHASE) return GNA_EINVAL;
+    if (d->kind != GNA_PEARSON && d->kind != GNA_POISSON) return GNA_EINVAL;
+    for (int i = 0; i < d->nbins; i++)
+        if (!(d->edges[i] > 0.0) || !(d->edges[i + 1] > d->edges[i])) return GNA_EINVAL;
+    for (int r = 0; r < d->nL; r++)
+        if (!(d->L[r] > 0.0) || (d->Lweight && !(d->Lweight[r] >= 0.0))) return GNA_EINVAL;
+    for (int p = 0; p < d->npts; p++) {
+        const int n = d->node_counts ? d->node_counts[p] : d->nodes_per_bin;
+        if (n < 1 || n > GNA_MAX_ORDER) return GNA_ESHAPE;
+        if (!d->node_counts) break;
+    }
+    if (!(d->norm > 0.0)) return GNA_EINVAL;
+    gna_plan* plan = new gna_plan();
+    gna_status st = plan_build(plan, d, (cudaStream_t)stream);
+    if (st != GNA_OK) {
+        fprintf(stderr, "gna_plan_create: %s\n", plan->err.c_str());
+        cudaStreamSynchronize((cudaStream_t)stream);
+        gna_plan_destroy(plan);
+        return st;
+    }
+    *out = plan;
+    return GNA_OK;
+}
+
+gna_status gna_plan_status(gna_plan* plan) {
+    if (!plan) return GNA_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "asynchronous CUDA error: %s", cudaGetErrorString(e));
+    int st = 0;
+    e = cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "status read: %s", cudaGetErrorString(e));
+    if (st != 0) {
+        cudaMemset(plan->d_status, 0, sizeof(int));
+        return fail(plan, (gna_status)st, "device status %d", st);
+    }
+    return GNA_OK;
+}
+
+gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta, const double* data,
+                          int data_per_point, const gna_outputs* out, void* stream) {
+    TRY(check_eval_args(plan, params, data, out, data_per_point));
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    EvalReq q{params, eta, sigma_eta, data, data_per_point, out->chi2, out->grad, out->grad_eta, out->mu, out->spectra,
+              nullptr};
+    if (!plan->use_graph) return enqueue_eval(plan, q, s, &plan->last_launches);
+    double sig = sigma_eta;
+    uintptr_t sigbits;
+    memcpy(&sigbits, &sig, sizeof(sigbits));
+    GraphKey key{{(uintptr_t)params, (uintptr_t)eta, sigbits, (uintptr_t)data, (uintptr_t)data_per_point,
+                  (uintptr_t)out->chi2, (uintptr_t)out->grad, (uintptr_t)out->grad_eta, (uintptr_t)out->mu,
+                  (uintptr_t)out->spectra, (uintptr_t)plan->block, (uintptr_t)plan->npt, (uintptr_t)plan->grid_mult}};
+    if (!plan->gexec || !(key == plan->gkey)) {
+        destroy_graph(plan);
+        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int nl = 0;
+        gna_status st = enqueue_eval(plan, q, s, &nl);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != GNA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&plan->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            plan->gexec = nullptr;
+            return fail(plan, GNA_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        plan->gkey = key;
+        plan->graph_launches = nl;
+    }
+    CU(cudaGraphLaunch(plan->gexec, s));
+    plan->last_launches = plan->graph_launches;
+    return GNA_OK;
+}
+
+gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                               const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
+                               void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (spectra && !plan->d_spec_stage) return fail(plan, GNA_ESHAPE, "spectra staging exceeds 2^24 values");
+    if (!params || !data || !chi2) return fail(plan, GNA_EINVAL, "params, data and chi2 are required");
+    if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t drows = data_per_point ? (size_t)plan->npts : 1;
+    CU(cudaMemcpyAsync(plan->d_params_stage, params, sizeof(gna_osc) * plan->npts, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(plan->d_data_stage, data, sizeof(double) * drows * plan->nbins, cudaMemcpyHostToDevice, s));
+    if (eta) CU(cudaMemcpyAsync(plan->d_eta_stage, eta, sizeof(double) * plan->nbins, cudaMemcpyHostToDevice, s));
+    gna_outputs o{plan->d_chi2_stage, grad ? plan->d_grad_stage : nullptr, nullptr, nullptr,
+                  spectra ? plan->d_spec_stage : nullptr};
+    TRY(gna_chain_eval(plan, plan->d_params_stage, eta ? plan->d_eta_stage : nullptr, sigma_eta, plan->d_data_stage,
+                       data_per_point, &o, stream));
+    CU(cudaMemcpyAsync(chi2, plan->d_chi2_stage, sizeof(double) * plan->npts, cudaMemcpyDeviceToHost, s));
+    if (grad) CU(cudaMemcpyAsync(grad, plan->d_grad_stage, sizeof(double) * 4 * plan->npts, cudaMemcpyDeviceToHost, s));
+    if (spectra)
+        CU(cudaMemcpyAsync(spectra, plan->d_spec_stage, sizeof(double) * plan->npts * plan->nL * plan->nbins,
+                           cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return GNA_OK;
+}
+
+gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                                const double* data, int data_per_point, const gna_outputs* out, void* stream) {
+    TRY(check_eval_args(plan, params, data, out, data_per_point));
+    if (!plan->plain64 || !plan->d_plainP)
+        return fail(plan, GNA_ESTATE, "plan was created without GNA_PLAN_WITH_PLAIN");
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    const bool grad = out->grad || out->grad_eta;
+    CU(launch_prepare(params, plan->npts, plan->bc, plan->d_pc, s));
+    int nl = 1;
+    for (int p = 0; p < plan->npts; p++) {
+        PlainChi2Args ca{};
+        ca.mu_r = plan->d_plainMu;
+        ca.dmu = grad ? plan->d_plainDmu : nullptr;
+        ca.bc = plan->bc;
+        ca.nL = plan->nL;
+        ca.nbins = plan->nbins;
+        ca.norm = plan->norm;
+        ca.kind = plan->kind;
+        ca.eta = eta;
+        ca.sigma = sigma_eta;
+        ca.data = data + (data_per_point ? (size_t)p * plan->nbins : 0);
+        ca.chi2 = out->chi2 + p;
+        ca.grad = out->grad ? out->grad + 4 * (size_t)p : nullptr;
+        ca.mu_out = out->mu ? out->mu + (size_t)p * plan->nbins : nullptr;
+        ca.grad_eta_out = out->grad_eta ? out->grad_eta + (size_t)p * plan->nbins : nullptr;
+        ca.spectra_out = out->spectra ? out->spectra + (size_t)p * plan->nL * plan->nbins : nullptr;
+        CU(launch_plain_point(plan->plain64, plan->nbins, plan->n_uniform, plan->d_pc + p, plan->bc, plan->nL, grad,
+                              plan->d_plainP, plan->d_plainD, plan->d_plainMu, plan->d_plainDmu, ca, s));
+        nl += grad ? 6 : 4;
+    }
+    plan->last_launches = nl;
+    return GNA_OK;
+}
+
+gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, int iters, double lambda0, double* chi2_out,
+                         int use_graph, void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (!params || !data || !chi2_out) return fail(plan, GNA_EINVAL, "params, data and chi2_out are required");
+    if (iters < 1) return fail(plan, GNA_EINVAL, "iters must be >= 1");
+    if (plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "fits need one data row per point");
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    CU(launch_lm_init(plan->d_lm, plan->npts, lambda0, s));
+    EvalReq q{params, nullptr, 0.0, data, 1, plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr, plan->d_H};
+    int launches = 1;
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int nl = 0;
+        gna_status st = enqueue_eval(plan, q, s, &nl);
+        cudaError_t e1 = launch_lm_update(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, plan->d_lm, params,
+                                          chi2_out, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != GNA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e1 != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(plan, GNA_ECUDA, "fit graph capture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e));
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "fit graph instantiate: %s", cudaGetErrorString(e));
+        for (int it = 0; it < iters; it++) {
+            e = cudaGraphLaunch(ex, s);
+            if (e != cudaSuccess) break;
+        }
+        cudaGraphExecDestroy(ex);
+        if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "fit graph launch: %s", cudaGetErrorString(e));
+        launches += iters * (nl + 1);
+    } else {
+        for (int it = 0; it < iters; it++) {
+            int nl = 0;
+            TRY(enqueue_eval(plan, q, s, &nl));
+            CU(launch_lm_update(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, plan->d_lm, params, chi2_out, s));
+            launches += nl + 1;
+        }
+    }
+    CU(launch_lm_finish(plan->npts, plan->d_lm, params, s));
+    plan->last_launches = launches + 1;
+    return GNA_OK;
+}
+
+gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen) {
+    if (!plan || !buf || buflen < 1) return GNA_EINVAL;
+    snprintf(buf, buflen, "mapping=%s block=%d nodes=%d grid=%d", plan->mapping == MAP_SPLIT ? "split" : "bins",
+             plan->block, plan->npt, plan->grid_mult);
+    return GNA_OK;
+}
+
+gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
+    if (!plan || !text) return GNA_EINVAL;
+    int block = plan->block, npt = plan->npt, gm = plan->grid_mult;
+    const char* b = strstr(text, "block=");
+    const char* n = strstr(text, "nodes=");
+    const char* g = strstr(text, "grid=");
+    if (b) block = atoi(b + 6);
+    if (n) npt = atoi(n + 6);
+    if (g) gm = atoi(g + 5);
+    if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64)
+        return fail(plan, GNA_EINVAL, "bad tuning '%s'", text);
+    if (plan->mapping == MAP_SPLIT) {
+        const int chunk = block * npt;
+        const int nch = (plan->n_uniform + chunk - 1) / chunk;
+        if ((size_t)plan->npts * plan->nbins * nch * fused_nv(plan->nl_inst, true, true) > plan->part_cap)
+            return fail(plan, GNA_ESHAPE, "tile %d x %d needs more partials than allocated", block, npt);
+    }
+    plan->block = block;
+    plan->npt = npt;
+    plan->grid_mult = gm;
+    destroy_graph(plan);
+    return GNA_OK;
+}
+
+gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point, int reps,
+                             void* stream) {
+    if (!plan || !params || !data) return GNA_EINVAL;
+    if (reps < 1) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool graph = plan->use_graph;
+    plan->use_graph = false;
+    std::vector<std::pair<int, int>> cand;
+    const int blocks[3] = {64, 128, 256};
+    if (plan->mapping == MAP_SPLIT) {
+        const int npts_c[6] = {4, 8, 16, 32, 64, 128};
+        for (int b : blocks)
+            for (int m : npts_c) {
+                const int chunk = b * m;
+                if (chunk > 4 * plan->n_uniform && m > 4) continue;
+                cand.push_back({b, m});
+            }
+    } else {
+        for (int b : blocks) cand.push_back({b, 1});
+    }
+    const int old_block = plan->block, old_npt = plan->npt;
+    float best = 1e30f;
+    int bb = old_block, bm = old_npt;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    gna_outputs o{plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr};
+    for (auto& c : cand) {
+        char t[64];
+        snprintf(t, sizeof(t), "block=%d nodes=%d", c.first, c.second);
+        if (gna_plan_set_tuning(plan, t) != GNA_OK) continue;
+        gna_status st = gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);  // warm-up
+        if (st != GNA_OK) continue;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; r++) gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bb = c.first;
+            bm = c.second;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->use_graph = graph;
+    char t[64];
+    snprintf(t, sizeof(t), "block=%d nodes=%d", bb, bm);
+    gna_status st = gna_plan_set_tuning(plan, t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    return st;
+}
+
+gna_status gna_plan_set_graph(gna_plan* plan, int on) {
+    if (!plan) return GNA_EINVAL;
+    plan->use_graph = on != 0;
+    if (!plan->use_graph) destroy_graph(plan);
+    return GNA_OK;
+}
+
+int gna_plan_kernel_launches(const gna_plan* plan) { return plan ? plan->last_launches : 0; }
+
+gna_status gna_plan_profile(gna_plan* plan, int on) {
+    if (!plan) return GNA_EINVAL;
+    destroy_profile(plan);
+    if (on) {
+        plan->prof_ev.resize(2 * 8192);
+        for (auto& e : plan->prof_ev) CU(cudaEventCreate(&e));
+        plan->profile = true;
+    }
+    return GNA_OK;
+}
+
+gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches) {
+    if (!plan || !total_ms || !launches) return GNA_EINVAL;
+    double tot = 0.0;
+    for (int i = 0; i < plan->prof_n; i++) {
+        CU(cudaEventSynchronize(plan->prof_ev[2 * i + 1]));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, plan->prof_ev[2 * i], plan->prof_ev[2 * i + 1]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = plan->prof_n;
+    plan->prof_n = 0;
+    return GNA_OK;
+}
+
+gna_status gna_plan_set_wait_limit(gna_plan* plan, int64_t limit) {
+    if (!plan || limit < 0) return GNA_EINVAL;
+    plan->wait_limit = limit;
+    return GNA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,554 @@
+// kernels_misc.cu -- everything on the device except the fused node loop:
+// parameter preparation (step a0), the Gauss-Legendre rule and energy grids
+// (step a1, configuration stage), the chi^2 epilogue (steps a7-a9), the plain
+// FP64 one-kernel-per-transformation chain, the element-wise OscProb
+// transformation and the Levenberg-Marquardt update.
+#include <math.h>
+
+#include "common.cuh"
+#include "gnaosc.h"
+#include "misc.h"
+
+namespace gna {
+
+// --------------------------------------------------------------- step a0 --
+// |U_e1|^2 = (1-s12)(1-s13), |U_e2|^2 = s12 (1-s13), |U_e3|^2 = s13 give
+// A21 = 4 s12 (1-s12)(1-s13)^2, A31 = 4 (1-s12)(1-s13) s13, A32 = 4 s12 (1-s13) s13
+// and their derivatives with respect to s12 = sin^2 theta12, s13 = sin^2 theta13.
+__device__ void prepare_point(const gna_osc& o, const BaseConst& bc, PointConst& pc) {
+    const double s12 = o.s2_12, s13 = o.s2_13;
+    const double c12 = 1.0 - s12, c13 = 1.0 - s13;
+    pc.A[0] = 4.0 * s12 * c12 * c13 * c13;
+    pc.A[1] = 4.0 * c12 * c13 * s13;
+    pc.A[2] = 4.0 * s12 * c13 * s13;
+    pc.dA12[0] = 4.0 * (1.0 - 2.0 * s12) * c13 * c13;
+    pc.dA12[1] = -4.0 * c13 * s13;
+    pc.dA12[2] = 4.0 * c13 * s13;
+    pc.dA13[0] = -8.0 * s12 * c12 * c13;
+    pc.dA13[1] = 4.0 * c12 * (1.0 - 2.0 * s13);
+    pc.dA13[2] = 4.0 * s12 * (1.0 - 2.0 * s13);
+    for (int j = 0; j < 3; j++) {
+        pc.Af[j] = (float)pc.A[j];
+        pc.dA12f[j] = (float)pc.dA12[j];
+        pc.dA13f[j] = (float)pc.dA13[j];
+    }
+    for (int r = 0; r < GNA_NLMAX; r++) {
+        const double kl = (r < bc.nL) ? bc.kld[r] : 0.0;
+        pc.c21[r] = o.dm2_21 * kl;
+        pc.c32[r] = o.dm2_32 * kl;
+        split_ff(pc.c21[r], pc.c21h[r], pc.c21l[r]);
+        split_ff(pc.c32[r], pc.c32h[r], pc.c32l[r]);
+    }
+    pc.pad[0] = pc.pad[1] = pc.pad[2] = 0.f;
+}
+
+__global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, BaseConst bc, PointConst* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    PointConst pc;
+    prepare_point(prm[p], bc, pc);
+    out[p] = pc;
+}
+
+cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s) {
+    k_prepare_points<<<(npts + 127) / 128, 128, 0, s>>>(prm, npts, bc, out);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- step a1 --
+// Gauss-Legendre rule of order n: Newton iteration on P_n evaluated by the
+// three-term recurrence P_{j+1} = a_j x P_j - b_j P_{j-1}, a_j = (2j+1)/(j+1),
+// b_j = j/(j+1) (tabulated once per order), from Tricomi's asymptotic
+// estimate of the k-th root; P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1);
+// w = 2 / ((1 - x^2) P_n'(x)^2), with 1 - x^2 formed as (1 - x)(1 + x).
+// One thread per root pair (x, -x).
+__global__ void k_legendre_coef(int n, double* __restrict__ a, double* __restrict__ b) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    a[j] = (2.0 * j + 1.0) / (j + 1.0);
+    b[j] = (double)j / (j + 1.0);
+}
+
+__device__ __forceinline__ void legendre_pair(int n, double x, const double* __restrict__ a, const double* __restrict__ b,
+                                              double& pn, double& pn1) {
+    double p0 = 1.0, p1 = x;
+    for (int j = 1; j < n; j++) {
+        const double p2 = a[j] * x * p1 - b[j] * p0;
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = (n == 0) ? 1.0 : p1;
+    pn1 = (n == 0) ? 0.0 : p0;
+}
+
+__global__ void k_gl_roots(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ x,
+                           double* __restrict__ w) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k-th largest root, 0-based
+    const int half = (n + 1) / 2;
+    if (k >= half) return;
+    const double nn = (double)n;
+    const double theta = M_PI * (4.0 * k + 3.0) / (4.0 * nn + 2.0);
+    double xk = (1.0 - (nn - 1.0) / (8.0 * nn * nn * nn)) * cos(theta);
+    if ((n & 1) && k == half - 1) xk = 0.0;  // middle root of odd orders
+    double pn = 0, pn1 = 0, dp = 1;
+    for (int it = 0; it < 12; it++) {
+        legendre_pair(n, xk, a, b, pn, pn1);
+        dp = nn * (xk * pn - pn1) / ((xk - 1.0) * (xk + 1.0));
+        const double dx = pn / dp;
+        xk -= dx;
+        if (fabs(dx) <= 2e-16 * fabs(xk) + 1e-300) break;
+    }
+    if ((n & 1) && k == half - 1) xk = 0.0;
+    legendre_pair(n, xk, a, b, pn, pn1);
+    dp = nn * (xk * pn - pn1) / ((xk - 1.0) * (xk + 1.0));
+    const double wk = 2.0 / (((1.0 - xk) * (1.0 + xk)) * dp * dp);  // 1 - x^2 without cancellation near +-1
+    x[n - 1 - k] = xk;
+    w[n - 1 - k] = wk;
+    x[k] = -xk;
+    w[k] = wk;
+}
+
+cudaError_t launch_gl(int n, double* x, double* w, double* tmp_ab /*[2n]*/, cudaStream_t s) {
+    k_legendre_coef<<<(n + 255) / 256, 256, 0, s>>>(n, tmp_ab, tmp_ab + n);
+    const int half = (n + 1) / 2;
+    k_gl_roots<<<(half + 63) / 64, 64, 0, s>>>(n, tmp_ab, tmp_ab + n, x, w);
+    return cudaGetLastError();
+}
+
+// Energy grid of one point: E_ik = (a_i+b_i)/2 + (b_i-a_i)/2 x_k, stored as
+// 1/E split into two floats, W = (b_i-a_i)/2 w_k S(E_ik e_scale) with the
+// reactor shape S(E) = exp(0.87 - 0.16 E - 0.091 E^2), and W/E.  Layout 0:
+// bin-major (node k of bin i at i*n + k); layout 1: groups of 32 bins,
+// node k of bin i at ((i/32) n + k) 32 + i%32, padded bins have W = 0.
+__global__ void k_build_grid(int nbins, int nbins_pad, const double* __restrict__ edges, int n, const double* __restrict__ x,
+                             const double* __restrict__ w, double e_scale, int layout, float4* __restrict__ ff,
+                             double2* __restrict__ d64, double2* __restrict__ plain64) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nbins_pad * n) return;
+    const int i = (int)(idx / n);
+    const int k = (int)(idx - (int64_t)i * n);
+    double invE = 1.0, Wd = 0.0;
+    if (i < nbins) {
+        const double a = edges[i], b = edges[i + 1];
+        const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+        const double E = mid + half * x[k];
+        const double Es = E * e_scale;
+        invE = 1.0 / E;
+        Wd = half * w[k] * exp(0.87 - 0.16 * Es - 0.091 * Es * Es);
+    }
+    const int64_t pos = (layout == 0) ? idx : (((int64_t)(i >> 5) * n + k) * 32 + (i & 31));
+    if (ff) {
+        float hi, lo;
+        split_ff(invE, hi, lo);
+        ff[pos] = make_float4(hi, lo, (float)Wd, (float)(Wd * invE));
+    }
+    if (d64) d64[pos] = make_double2(invE, Wd);
+    if (plain64 && i < nbins) plain64[idx] = make_double2(invE, Wd);
+}
+
+cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int n, const double* x, const double* w,
+                              double e_scale, int layout, float4* ff, double2* d64, double2* plain64, cudaStream_t s) {
+    const int64_t total = (int64_t)nbins_pad * n;
+    const int64_t blocks = (total + 255) / 256;
+    k_build_grid<<<(unsigned)blocks, 256, 0, s>>>(nbins, nbins_pad, edges, n, x, w, e_scale, layout, ff, d64, plain64);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ steps a7-a9 --
+// Per (point, bin): sum the node-chunk partials, form
+//   M_i = sum_r omega_r mu_r,i,  mu_i = N (1 + eta_i) M_i,
+//   Pearson chi2_i = (d - mu)^2 / mu,  g_i = 1 - d^2 / mu^2,
+//   Poisson chi2_i = 2 (mu - d + d ln(d/mu)) (2 mu if d = 0), g_i = 2 (1 - d/mu),
+// plus eta_i^2 / sigma^2, the gradient terms g_i N (1+eta_i) dM_i/dtheta and,
+// for the fitter, (2 / mu_i) J_i J_i^T with J_i = N (1+eta_i) dM_i/dtheta.
+__global__ void k_epi_bin(EpiArgs a) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)a.npts * a.nbins) return;
+    const int p = (int)(idx / a.nbins);
+    const int i = (int)(idx - (int64_t)p * a.nbins);
+    double v[GNA_NV_BASE + GNA_NLMAX];
+    for (int j = 0; j < a.NV; j++) v[j] = 0.0;
+    if (a.is64) {
+        const double* src = (const double*)a.part + idx * a.nchunks * a.NV;
+        for (int c = 0; c < a.nchunks; c++)
+            for (int j = 0; j < a.NV; j++) v[j] += src[c * a.NV + j];
+    } else {
+        const float2* src = (const float2*)a.part + idx * a.nchunks * a.NV;
+        for (int c = 0; c < a.nchunks; c++)
+            for (int j = 0; j < a.NV; j++) {
+                const float2 f = src[c * a.NV + j];
+                v[j] += (double)f.x + (double)f.y;
+            }
+    }
+    const double M = v[0];
+    const double e = a.eta ? a.eta[i] : 0.0;
+    const double f = a.norm * (1.0 + e);
+    const double mu = f * M;
+    const double d = a.data[a.data_per_point ? idx : i];
+    double term, g;
+    if (a.kind == GNA_PEARSON) {
+        term = (d - mu) * (d - mu) / mu;
+        g = 1.0 - (d * d) / (mu * mu);
+    } else {
+        term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
+        g = 2.0 * (1.0 - d / mu);
+    }
+    const bool pen = a.eta && a.sigma > 0.0;
+    if (pen) term += e * e / (a.sigma * a.sigma);
+    double* bv = a.binvals + idx * a.NBV;
+    bv[0] = term;
+    if (a.has_grad && a.NBV >= 5) {
+        double J[4];
+        for (int q = 0; q < 4; q++) {
+            J[q] = -f * v[1 + q];
+            bv[1 + q] = g * J[q];
+        }
+        if (a.NBV >= 15) {
+            const double h = 2.0 / mu;
+            int t = 5;
+            for (int q = 0; q < 4; q++)
+                for (int r = q; r < 4; r++) bv[t++] = h * J[q] * J[r];
+        }
+    }
+    if (a.mu_out) a.mu_out[idx] = mu;
+    if (a.grad_eta_out) a.grad_eta_out[idx] = g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
+    if (a.spectra_out && a.nspec > 0) {
+        const int off = 1 + (a.has_grad ? 4 : 0);
+        for (int r = 0; r < a.nL_out; r++) a.spectra_out[((int64_t)p * a.nL_out + r) * a.nbins + i] = v[off + r];
+    }
+}
+
+// Per point: fixed-order tree sum over bins of the per-bin values.
+__global__ void k_epi_point(const double* __restrict__ binvals, int nbins, int NBV, double* __restrict__ chi2,
+                            double* __restrict__ grad, double* __restrict__ H) {
+    __shared__ double sh[256];
+    const int p = blockIdx.x;
+    const double* bv = binvals + (int64_t)p * nbins * NBV;
+    for (int v = 0; v < NBV; v++) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) s += bv[(int64_t)i * NBV + v];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double tot = sh[0];
+            if (v == 0) {
+                if (chi2) chi2[p] = tot;
+            } else if (v < 5) {
+                if (grad) grad[(int64_t)p * 4 + v - 1] = tot;
+            } else if (H) {
+                H[(int64_t)p * 10 + v - 5] = tot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_epilogue(const EpiArgs& a, double* chi2, double* grad, double* H, cudaStream_t s) {
+    const int64_t total = (int64_t)a.npts * a.nbins;
+    k_epi_bin<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(a);
+    k_epi_point<<<a.npts, 256, 0, s>>>(a.binvals, a.nbins, a.NBV, chi2, grad, H);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- plain FP64 chain -------
+// One kernel per transformation of the paper's chain, intermediates in
+// device memory: OscProb (+ tangents) -> weight -> bin integration -> chi^2.
+__global__ void k_plain_prob(const double2* __restrict__ nodes, int64_t nn, const PointConst* __restrict__ pcp, BaseConst bc,
+                             int nL, int grad, double* __restrict__ P, double* __restrict__ dP) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nn * nL) return;
+    const int r = (int)(idx / nn);
+    const int64_t k = idx - (int64_t)r * nn;
+    const PointConst& pc = *pcp;
+    const double e = nodes[k].x;
+    const double x21 = pc.c21[r] * e, x32 = pc.c32[r] * e, x31 = (pc.c21[r] + pc.c32[r]) * e;
+    double s21, c21, s31, c31, s32, c32;
+    sincos(x21, &s21, &c21);
+    sincos(x31, &s31, &c31);
+    sincos(x32, &s32, &c32);
+    const double S21 = s21 * s21, S31 = s31 * s31, S32 = s32 * s32;
+    P[idx] = 1.0 - pc.A[0] * S21 - pc.A[1] * S31 - pc.A[2] * S32;
+    if (grad) {
+        const int64_t stride = nn * nL;
+        const double kle = bc.kld[r] * e;
+        dP[idx] = -(pc.dA12[0] * S21 + pc.dA12[1] * S31 + pc.dA12[2] * S32);
+        dP[stride + idx] = -(pc.dA13[0] * S21 + pc.dA13[1] * S31 + pc.dA13[2] * S32);
+        dP[2 * stride + idx] = -(pc.A[0] * 2.0 * s21 * c21 + pc.A[1] * 2.0 * s31 * c31) * kle;
+        dP[3 * stride + idx] = -(pc.A[1] * 2.0 * s31 * c31 + pc.A[2] * 2.0 * s32 * c32) * kle;
+    }
+}
+
+__global__ void k_plain_weight(const double2* __restrict__ nodes, int64_t nn, int64_t rows, double* __restrict__ V) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nn * rows) return;
+    V[idx] *= nodes[idx % nn].y;
+}
+
+// one warp per (row, bin)
+__global__ void k_plain_binint(const double* __restrict__ V, int64_t rows, int nbins, int n, double* __restrict__ out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= rows * nbins) return;
+    const int64_t row = w / nbins;
+    const int i = (int)(w - row * nbins);
+    const double* src = V + row * (int64_t)nbins * n + (int64_t)i * n;
+    double s = 0.0;
+    for (int k = lane; k < n; k += 32) s += src[k];
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[w] = s;
+}
+
+// one CTA per point; mu_r [nL][nbins], dmu [4][nL][nbins]
+__global__ void k_plain_chi2(PlainChi2Args a) {
+    __shared__ double sh[5][256];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+        double M = 0, D[4] = {0, 0, 0, 0};
+        for (int r = 0; r < a.nL; r++) {
+            M += a.bc.omd[r] * a.mu_r[(int64_t)r * a.nbins + i];
+            if (a.dmu)
+                for (int q = 0; q < 4; q++) D[q] += a.bc.omd[r] * a.dmu[((int64_t)q * a.nL + r) * a.nbins + i];
+        }
+        const double e = a.eta ? a.eta[i] : 0.0;
+        const double f = a.norm * (1.0 + e);
+        const double mu = f * M;
+        const double d = a.data[i];
+        double term, g;
+        if (a.kind == GNA_PEARSON) {
+            term = (d - mu) * (d - mu) / mu;
+            g = 1.0 - (d * d) / (mu * mu);
+        } else {
+            term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
+            g = 2.0 * (1.0 - d / mu);
+        }
+        const bool pen = a.eta && a.sigma > 0.0;
+        if (pen) term += e * e / (a.sigma * a.sigma);
+        acc[0] += term;
+        for (int q = 0; q < 4; q++) acc[1 + q] += g * f * D[q];
+        if (a.mu_out) a.mu_out[i] = mu;
+        if (a.grad_eta_out) a.grad_eta_out[i] = g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
+        if (a.spectra_out)
+            for (int r = 0; r < a.nL; r++) a.spectra_out[(int64_t)r * a.nbins + i] = a.mu_r[(int64_t)r * a.nbins + i];
+    }
+    for (int v = 0; v < 5; v++) sh[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int v = 0; v < 5; v++) sh[v][threadIdx.x] += sh[v][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.chi2[0] = sh[0][0];
+        if (a.grad)
+            for (int q = 0; q < 4; q++) a.grad[q] = sh[1 + q][0];
+    }
+}
+
+cudaError_t launch_plain_point(const double2* nodes, int nbins, int n, const PointConst* pc, const BaseConst& bc, int nL,
+                               int grad, double* P, double* dP, double* mu_r, double* dmu, const PlainChi2Args& ca,
+                               cudaStream_t s) {
+    const int64_t nn = (int64_t)nbins * n;
+    const int64_t t1 = nn * nL;
+    k_plain_prob<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(nodes, nn, pc, bc, nL, grad, P, dP);
+    k_plain_weight<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(nodes, nn, nL, P);
+    if (grad) k_plain_weight<<<(unsigned)((4 * t1 + 255) / 256), 256, 0, s>>>(nodes, nn, 4 * nL, dP);
+    const int64_t w1 = (int64_t)nL * nbins * 32;
+    k_plain_binint<<<(unsigned)((w1 + 255) / 256), 256, 0, s>>>(P, nL, nbins, n, mu_r);
+    if (grad) k_plain_binint<<<(unsigned)((4 * w1 + 255) / 256), 256, 0, s>>>(dP, 4 * nL, nbins, n, dmu);
+    k_plain_chi2<<<1, 256, 0, s>>>(ca);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------- element-wise OscProb --
+// FP64: P[r][k] = 1 - sum_ij A_ij sin^2(c_ij,r / E_k), CUDA double sin.
+__global__ void k_oscprob64(const double* __restrict__ E, int64_t n, OscConst oc, double* __restrict__ P) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double e = 1.0 / E[k];
+    for (int r = 0; r < oc.nL; r++) {
+        const double s21 = sin(oc.c21[r] * e), s32 = sin(oc.c32[r] * e), s31 = sin((oc.c21[r] + oc.c32[r]) * e);
+        P[(int64_t)r * n + k] = 1.0 - oc.A[0] * s21 * s21 - oc.A[1] * s31 * s31 - oc.A[2] * s32 * s32;
+    }
+}
+
+// Mixed: each phase reduced modulo pi/2 (quadrant parity q), sin r by the
+// FP32 polynomial; sin^2(phase) = s^2 for even q, 1 - s^2 for odd q.  The
+// dominant term is written as (1 - A21) + A21 s^2 for odd q so that P stays
+// accurate to a few ulp where it is smallest.
+template <int PH>
+__device__ __forceinline__ float reduce_half_pi(float ch, float cl, double cd, float eh, float el, double ed, int& odd) {
+    if (PH == 0) {
+        float p = __fmul_rn(ch, eh);
+        float e = __fmaf_rn(ch, eh, -p);
+        float lo = __fmaf_rn(ch, el, __fmaf_rn(cl, eh, e));
+        float qm = __fmaf_rn(p, 2.0f * GNA_INV_PI_F, GNA_ROUND_MAGIC);
+        odd = __float_as_int(qm) & 1;
+        float q = __fsub_rn(qm, GNA_ROUND_MAGIC);
+        float r = __fmaf_rn(-q, 0.5f * GNA_PI_A, p);
+        r = __fmaf_rn(-q, 0.5f * GNA_PI_B, r);
+        r = __fmaf_rn(-q, 0.5f * GNA_PI_C, r);
+        return __fadd_rn(r, lo);
+    } else {
+        double p = cd * ed;
+        double q = rint(p * (2.0 * GNA_INV_PI_D));
+        odd = ((long long)q) & 1;
+        double r = fma(-q, 0.5 * GNA_PI_DA, p);
+        r = fma(-q, 0.5 * GNA_PI_DB, r);
+        r = fma(-q, 0.5 * GNA_PI_DC, r);
+        return (float)r;
+    }
+}
+
+template <int PH>
+__global__ void k_oscprob_mixed(const double* __restrict__ E, int64_t n, OscConst oc, float* __restrict__ P) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double ed = 1.0 / E[k];
+    float eh, el;
+    split_ff(ed, eh, el);
+    const float A21 = oc.Af[0], A31 = oc.Af[1], A32 = oc.Af[2];
+    const float omA21 = oc.one_minus_A21f;
+    for (int r = 0; r < oc.nL; r++) {
+        int o21, o31, o32;
+        const float r21 = reduce_half_pi<PH>(oc.c21h[r], oc.c21l[r], oc.c21[r], eh, el, ed, o21);
+        const float r31 = reduce_half_pi<PH>(oc.c31h[r], oc.c31l[r], oc.c21[r] + oc.c32[r], eh, el, ed, o31);
+        const float r32 = reduce_half_pi<PH>(oc.c32h[r], oc.c32l[r], oc.c32[r], eh, el, ed, o32);
+        const float s21 = sin_poly(r21), s31 = sin_poly(r31), s32 = sin_poly(r32);
+        const float q21 = s21 * s21, q31 = s31 * s31, q32 = s32 * s32;
+        const float S31 = o31 ? 1.0f - q31 : q31;
+        const float S32 = o32 ? 1.0f - q32 : q32;
+        const float base = o21 ? fmaf(A21, q21, omA21) : fmaf(-A21, q21, 1.0f);
+        P[(int64_t)r * n + k] = fmaf(-A32, S32, fmaf(-A31, S31, base));
+    }
+}
+
+cudaError_t launch_oscprob(const double* E, int64_t n, const OscConst& oc, int prec, void* P, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (prec == GNA_FP64)
+        k_oscprob64<<<blocks, 256, 0, s>>>(E, n, oc, (double*)P);
+    else if (prec == GNA_MIXED_F64PHASE)
+        k_oscprob_mixed<1><<<blocks, 256, 0, s>>>(E, n, oc, (float*)P);
+    else
+        k_oscprob_mixed<0><<<blocks, 256, 0, s>>>(E, n, oc, (float*)P);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ Levenberg-Marquardt ----
+// Per dataset: accept the evaluated trial if chi2 improved (lambda /= 10)
+// else reject it (lambda *= 10); solve (H + lambda diag H) delta = -g at the
+// best point (Gaussian elimination, partial pivoting) and clamp the next trial.
+__global__ void k_lm_init(LMState* __restrict__ st, int npts, double lam0) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    LMState s;
+    for (int q = 0; q < 4; q++) {
+        s.best[q] = 0.0;
+        s.g[q] = 0.0;
+    }
+    for (int q = 0; q < 10; q++) s.H[q] = 0.0;
+    s.chi2 = HUGE_VAL;
+    s.lam = lam0;
+    st[p] = s;
+}
+
+__global__ void k_lm_update(int npts, const double* __restrict__ chi2, const double* __restrict__ grad,
+                            const double* __restrict__ H, LMState* __restrict__ st, gna_osc* __restrict__ prm,
+                            double* __restrict__ chi2_best) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    LMState s = st[p];
+    const gna_osc t = prm[p];
+    const double th[4] = {t.s2_12, t.s2_13, t.dm2_21, t.dm2_32};
+    const double c = chi2[p];
+    if (c < s.chi2) {
+        s.chi2 = c;
+        for (int q = 0; q < 4; q++) {
+            s.best[q] = th[q];
+            s.g[q] = grad[(int64_t)p * 4 + q];
+        }
+        for (int q = 0; q < 10; q++) s.H[q] = H[(int64_t)p * 10 + q];
+        s.lam = s.lam / 10.0;
+    } else {
+        s.lam = s.lam * 10.0;
+    }
+    double A[4][5];
+    int t10 = 0;
+    for (int q = 0; q < 4; q++)
+        for (int r = q; r < 4; r++) {
+            A[q][r] = s.H[t10];
+            A[r][q] = s.H[t10];
+            t10++;
+        }
+    for (int q = 0; q < 4; q++) {
+        A[q][q] += s.lam * A[q][q];
+        A[q][4] = -s.g[q];
+    }
+    bool ok = true;
+    for (int col = 0; col < 4; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 4; r++)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (!(fabs(A[piv][col]) > 0.0)) {
+            ok = false;
+            break;
+        }
+        if (piv != col)
+            for (int j = 0; j < 5; j++) {
+                const double tmp = A[col][j];
+                A[col][j] = A[piv][j];
+                A[piv][j] = tmp;
+            }
+        for (int r = col + 1; r < 4; r++) {
+            const double m = A[r][col] / A[col][col];
+            for (int j = col; j < 5; j++) A[r][j] -= m * A[col][j];
+        }
+    }
+    double delta[4] = {0, 0, 0, 0};
+    if (ok)
+        for (int q = 3; q >= 0; q--) {
+            double acc = A[q][4];
+            for (int j = q + 1; j < 4; j++) acc -= A[q][j] * delta[j];
+            delta[q] = acc / A[q][q];
+        }
+    const double lo[4] = {1e-6, 1e-6, 1e-7, 1e-7};
+    const double hi[4] = {1.0 - 1e-6, 1.0 - 1e-6, HUGE_VAL, HUGE_VAL};
+    double nx[4];
+    for (int q = 0; q < 4; q++) nx[q] = fmin(fmax(s.best[q] + delta[q], lo[q]), hi[q]);
+    prm[p].s2_12 = nx[0];
+    prm[p].s2_13 = nx[1];
+    prm[p].dm2_21 = nx[2];
+    prm[p].dm2_32 = nx[3];
+    st[p] = s;
+    if (chi2_best) chi2_best[p] = s.chi2;
+}
+
+__global__ void k_lm_finish(int npts, const LMState* __restrict__ st, gna_osc* __restrict__ prm) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    prm[p].s2_12 = st[p].best[0];
+    prm[p].s2_13 = st[p].best[1];
+    prm[p].dm2_21 = st[p].best[2];
+    prm[p].dm2_32 = st[p].best[3];
+}
+
+cudaError_t launch_lm_init(LMState* st, int npts, double lam0, cudaStream_t s) {
+    k_lm_init<<<(npts + 127) / 128, 128, 0, s>>>(st, npts, lam0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMState* st, gna_osc* prm,
+                             double* chi2_best, cudaStream_t s) {
+    k_lm_update<<<(npts + 127) / 128, 128, 0, s>>>(npts, chi2, grad, H, st, prm, chi2_best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_finish(int npts, const LMState* st, gna_osc* prm, cudaStream_t s) {
+    k_lm_finish<<<(npts + 127) / 128, 128, 0, s>>>(npts, st, prm);
+    return cudaGetLastError();
+}
+
+}  // namespace gna

@@ -1,0 +1,78 @@
+// misc.h -- argument structs and launchers of kernels_misc.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "gnaosc.h"
+
+namespace gna {
+
+struct EpiArgs {
+    const void* part;  // float2 (mixed) or double (FP64) [npts][nbins][nchunks][NV]
+    int is64;
+    int nchunks, NV, has_grad, nspec, nL_out;
+    int npts, nbins;
+    double norm;
+    int kind;
+    const double* eta;
+    double sigma;
+    const double* data;
+    int data_per_point;
+    double* mu_out;
+    double* spectra_out;
+    double* grad_eta_out;
+    double* binvals;  // [npts][nbins][NBV]
+    int NBV;          // 1 (chi2), 5 (+ gradient), 15 (+ J^T W J)
+};
+
+struct PlainChi2Args {
+    const double* mu_r;  // [nL][nbins]
+    const double* dmu;   // [4][nL][nbins] or NULL
+    BaseConst bc;
+    int nL, nbins;
+    double norm;
+    int kind;
+    const double* eta;
+    double sigma;
+    const double* data;  // [nbins]
+    double* chi2;        // [1]
+    double* grad;        // [4] or NULL
+    double* mu_out;      // [nbins] or NULL
+    double* grad_eta_out;
+    double* spectra_out;  // [nL][nbins] or NULL
+};
+
+struct OscConst {
+    double c21[GNA_NLMAX], c32[GNA_NLMAX];
+    float c21h[GNA_NLMAX], c21l[GNA_NLMAX], c32h[GNA_NLMAX], c32l[GNA_NLMAX], c31h[GNA_NLMAX], c31l[GNA_NLMAX];
+    double A[3];
+    float Af[3];
+    float one_minus_A21f;
+    int nL;
+};
+
+struct LMState {
+    double best[4];
+    double chi2;
+    double g[4];
+    double H[10];
+    double lam;
+};
+
+cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s);
+cudaError_t launch_gl(int n, double* x, double* w, double* tmp_ab, cudaStream_t s);
+cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int n, const double* x, const double* w,
+                              double e_scale, int layout, float4* ff, double2* d64, double2* plain64, cudaStream_t s);
+cudaError_t launch_epilogue(const EpiArgs& a, double* chi2, double* grad, double* H, cudaStream_t s);
+cudaError_t launch_plain_point(const double2* nodes, int nbins, int n, const PointConst* pc, const BaseConst& bc, int nL,
+                               int grad, double* P, double* dP, double* mu_r, double* dmu, const PlainChi2Args& ca,
+                               cudaStream_t s);
+cudaError_t launch_oscprob(const double* E, int64_t n, const OscConst& oc, int prec, void* P, cudaStream_t s);
+cudaError_t launch_lm_init(LMState* st, int npts, double lam0, cudaStream_t s);
+cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMState* st, gna_osc* prm,
+                             double* chi2_best, cudaStream_t s);
+cudaError_t launch_lm_finish(int npts, const LMState* st, gna_osc* prm, cudaStream_t s);
+
+}  // namespace gna

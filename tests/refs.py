@@ -1,0 +1,49 @@
+"""Oracle-side references for the parity tests: every input and expected
+value here comes from the seeded generators and the FP64 oracle, never from
+the CUDA path."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_1804_07682_gb300 import workloads as wl
+
+
+class Case:
+    """A workload instance with oracle-derived normalisation and data."""
+
+    def __init__(self, w: wl.Workload, truth_nodes=None):
+        self.w = w
+        tn = truth_nodes if truth_nodes is not None else (w.nodes_per_bin or wl.SCAN_TRUTH_NODES)
+        self.omega = oracle.baseline_weights(w.L)
+        self.N = oracle.norm_for_total(w.edges, tn, w.L, w.truth, e_scale=w.e_scale)
+        self.mu_truth = self.N * (self.omega @ oracle.binned(w.edges, tn, w.L, w.truth, w.e_scale))
+        if w.n_datasets > 1:
+            self.data = wl.pseudo_datasets(self.mu_truth, w.n_datasets, w.data_seed)
+        else:
+            self.data = wl.poisson_data(self.mu_truth, w.data_seed)
+
+    def nodes_of(self, p):
+        w = self.w
+        return int(w.node_counts[p]) if w.node_counts is not None else w.nodes_per_bin
+
+    def data_of(self, p):
+        return self.data[p] if self.data.ndim == 2 else self.data
+
+    def oracle_point(self, p, grad=True, theta=None):
+        w = self.w
+        th = w.theta[p] if theta is None else theta
+        return oracle.chain(w.edges, self.nodes_of(p), w.L, th, self.N, self.data_of(p), w.kind, eta=w.eta,
+                            sigma=w.sigma_eta, e_scale=w.e_scale, grad=grad)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def normrel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -1,0 +1,257 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the workload definition): FP64 mode 1e-9 relative on chi^2,
+mu and spectra and 1e-9 normwise on the gradient; mixed modes 1e-6 relative on
+P, mu, spectra and chi^2 (gradient reported with a loose 1e-4 sanity bound).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1804_07682_gb300 import workloads as wl
+from refs import Case, normrel, rel
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+TOL = {"fp64": 1e-9, "f64phase": 1e-6, "ff": 1e-6}
+GTOL = {"fp64": 1e-9, "f64phase": 1e-4, "ff": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1804_07682_gb300 import api as _api
+    return _api
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def make_plan(api, case, prec, mapping=None, with_plain=False, per_point_data=False):
+    w = case.w
+    return api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, npts=w.npts, node_counts=w.node_counts,
+                    norm=case.N, e_scale=w.e_scale, prec=prec, kind=w.kind,
+                    max_datasets=w.npts if per_point_data else 0, with_plain=with_plain, mapping=mapping)
+
+
+# ------------------------------------------------------------ Gauss-Legendre
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 50, 262, 524, 4096, 16384])
+def test_gl_nodes(api, n):
+    x, w = api.gl_nodes(n)
+    xr, wr = oracle.gl(n)
+    x = x.cpu().numpy()
+    assert np.abs(x - xr).max() < 2e-15
+    # a one-ulp difference in a node moves its weight by ~4|x|/(1-x^2) ulp
+    tol = 1e-12 + 4 * np.spacing(1.0) * np.abs(xr) / ((1 - xr) * (1 + xr))
+    assert np.all(np.abs(w.cpu().numpy() / wr - 1) <= tol)
+
+
+# ------------------------------------------------------------------ OscProb
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
+@pytest.mark.parametrize("rng_case", ["reactor", "long_baseline"])
+def test_oscprob(api, prec, rng_case):
+    rng = np.random.default_rng(11)
+    if rng_case == "reactor":
+        E = rng.uniform(0.5, 15.0, 100003)
+        L = [0.5, 52.5, 60.0, 17.3]
+    else:
+        E = rng.uniform(500.0, 5000.0, 4099)
+        L = [810.0]
+    theta = (0.307, 0.0218, 7.53e-5, 2.44e-3 * 1.05)
+    P = api.oscprob(dev(E), L, theta, prec).double().cpu().numpy()
+    for r, Lr in enumerate(L):
+        ref = oracle.pee(E, Lr, theta)
+        assert rel(P[r], ref) < (1e-10 if prec == "fp64" else TOL[prec]), (prec, Lr)
+
+
+def test_oscprob_edge_cases(api):
+    E = dev([3.0])
+    P = api.oscprob(E, [0.0, 52.5], wl.TRUTH, "ff").cpu().numpy()
+    assert P[0, 0] == 1.0
+    assert abs(P[1, 0] - oracle.pee([3.0], 52.5, wl.TRUTH)[0]) < 1e-6
+    assert api.oscprob(dev(np.zeros(0)), [1.0], wl.TRUTH, "fp64").numel() == 0
+
+
+# ------------------------------------------------------- chain, small cases
+def small_cases():
+    return {
+        "reactor_200x50": lambda: wl.reactor_200x50(),
+        "reactor8_40x3000": lambda: wl.shrink(wl.reactor8_1000x16384(), nbins=40, nodes=3000),
+        "nuisance_64x1000": lambda: wl.shrink(wl.nuisance_1000x4096(), nbins=64, nodes=1000),
+        "scan_16pts_60bins": lambda: wl.shrink(wl.scan_64x64_500bins(4, 4), nbins=60),
+        "fits_8x100x20": lambda: wl.shrink(wl.fits_16384x1000(8), nbins=100, nodes=20),
+    }
+
+
+_case_cache = {}
+
+
+def get_case(name):
+    if name not in _case_cache:
+        w = small_cases()[name]()
+        tn = None if name != "scan_16pts_60bins" else 64
+        _case_cache[name] = Case(w, truth_nodes=tn)
+    return _case_cache[name]
+
+
+def check_chain(api, case, prec, mapping=None, spectra=True):
+    w = case.w
+    per_point = case.data.ndim == 2
+    plan = make_plan(api, case, prec, mapping, per_point_data=per_point)
+    eta = None if w.eta is None else dev(w.eta)
+    out = plan.eval(plan.params_tensor(w.theta), dev(case.data), eta, w.sigma_eta, grad=True,
+                    grad_eta=eta is not None, mu=True, spectra=spectra)
+    torch.cuda.synchronize()
+    plan.status()
+    tol, gtol = TOL[prec], GTOL[prec]
+    for p in range(w.npts):
+        ref = case.oracle_point(p)
+        assert rel(out["chi2"][p].item(), ref["chi2"]) < tol, (p, out["chi2"][p].item(), ref["chi2"])
+        assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < tol
+        if spectra:
+            assert rel(out["spectra"][p].cpu().numpy(), ref["mu_rb"]) < tol
+        assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:4]) < gtol
+        if eta is not None:
+            assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][4:]) < gtol
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
+@pytest.mark.parametrize("name", list(small_cases()))
+def test_chain_small(api, name, prec):
+    check_chain(api, get_case(name), prec)
+
+
+@pytest.mark.parametrize("mapping", ["split", "bins"])
+@pytest.mark.parametrize("name", ["reactor_200x50", "reactor8_40x3000", "fits_8x100x20"])
+def test_chain_both_mappings(api, name, mapping):
+    check_chain(api, get_case(name), "ff", mapping)
+
+
+@pytest.mark.parametrize("tuning", ["block=64 nodes=4", "block=128 nodes=7", "block=256 nodes=64", "block=96 nodes=3"])
+def test_chain_launch_shapes(api, tuning):
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, "ff", "split")
+    plan.tuning = tuning
+    out = plan.eval(plan.params_tensor(w.theta), dev(case.data), grad=True, mu=True)
+    ref = case.oracle_point(0)
+    assert rel(out["chi2"][0].item(), ref["chi2"]) < 1e-6
+    assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < 1e-6
+
+
+def test_chain_degenerate_shapes(api):
+    # one bin, one node per bin, one baseline; and zero-count bins in the data
+    w = wl.Workload("one", np.array([2.0, 2.5]), 1, np.array([52.5]), np.array([wl.TRUTH]), wl.POISSON)
+    case = Case(w)
+    case.data = np.array([0.0])
+    for prec in ("fp64", "ff"):
+        check_chain(api, case, prec)
+    w2 = wl.shrink(wl.reactor8_1000x16384(), nbins=33, nodes=1)
+    case2 = Case(w2)
+    for prec in ("fp64", "ff"):
+        check_chain(api, case2, prec)
+
+
+def test_plain_chain_matches_oracle(api):
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, "ff", with_plain=True)
+    out = plan.eval(plan.params_tensor(w.theta), dev(case.data), grad=True, mu=True, spectra=True, plain=True)
+    ref = case.oracle_point(0)
+    assert rel(out["chi2"][0].item(), ref["chi2"]) < 1e-9
+    assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < 1e-9
+    assert rel(out["spectra"][0].cpu().numpy(), ref["mu_rb"]) < 1e-9
+    assert normrel(out["grad"][0].cpu().numpy(), ref["grad"][:4]) < 1e-9
+
+
+def test_graph_replay_and_host_buffers(api):
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, "ff")
+    p = plan.params_tensor(w.theta)
+    d = dev(case.data)
+    a = plan.eval(p, d, grad=True)
+    a = {k: v.clone() for k, v in a.items()}
+    plan.set_graph(True)
+    outs = {"chi2": torch.empty(1, dtype=torch.float64, device="cuda"),
+            "grad": torch.empty(1, 4, dtype=torch.float64, device="cuda")}
+    for _ in range(3):
+        plan.eval(p, d, grad=True, out=outs)
+    torch.cuda.synchronize()
+    assert torch.equal(outs["chi2"], a["chi2"]) and torch.equal(outs["grad"], a["grad"])
+    assert plan.launches >= 4
+    c, g = plan.eval_host(w.theta, case.data, grad=True)
+    assert c[0] == a["chi2"][0].item() and np.array_equal(g, a["grad"].cpu().numpy())
+
+
+def test_autotune_keeps_parity(api):
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, "ff")
+    p = plan.params_tensor(w.theta)
+    d = dev(case.data)
+    text = plan.autotune(p, d, reps=2)
+    assert "block=" in text
+    out = plan.eval(p, d, grad=True)
+    ref = case.oracle_point(0)
+    assert rel(out["chi2"][0].item(), ref["chi2"]) < 1e-6
+
+
+def test_autograd_function(api):
+    case = get_case("nuisance_64x1000")
+    w = case.w
+    plan = make_plan(api, case, "fp64")
+    d = dev(case.data)
+    theta = dev(w.theta[0]).requires_grad_(True)
+    eta = dev(w.eta).requires_grad_(True)
+    c = api.chi2(theta, plan, d, eta, w.sigma_eta)
+    (2.0 * c).backward()
+    ref = case.oracle_point(0)
+    assert normrel(theta.grad.cpu().numpy(), 2.0 * ref["grad"][:4]) < 1e-9
+    assert normrel(eta.grad.cpu().numpy(), 2.0 * ref["grad"][4:]) < 1e-9
+
+    # FP64 central differences (h = 1e-6 relative) through the same plan
+    def f(t):
+        with torch.no_grad():
+            return api.chi2(dev(t), plan, d, dev(w.eta), w.sigma_eta).item()
+
+    g_fd = oracle.fd_grad(f, w.theta[0])
+    assert normrel(ref["grad"][:4], g_fd) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_fits_match_oracle(api, prec):
+    case = get_case("fits_8x100x20")
+    w = case.w
+    plan = make_plan(api, case, prec, per_point_data=True)
+    params = plan.params_tensor(w.theta).clone()
+    params, chi2 = plan.fit(params, dev(case.data), iters=20, graph=(prec == "ff"))
+    torch.cuda.synchronize()
+    plan.status()
+    P = params.cpu().numpy()
+    C = chi2.cpu().numpy()
+    for j in range(w.npts):
+        ev = lambda t, j=j: oracle.chain(w.edges, w.nodes_per_bin, w.L, t, case.N, case.data[j], w.kind)
+        th, c2, _ = oracle.fit_lm(ev, w.theta[j], iters=20)
+        assert rel(C[j], c2) < (1e-9 if prec == "fp64" else 1e-6), (j, C[j], c2)
+        assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
+
+
+def test_bad_arguments_raise(api):
+    from paper_1804_07682_gb300 import _native as N
+
+    case = get_case("reactor_200x50")
+    plan = make_plan(api, case, "ff")
+    p = plan.params_tensor(case.w.theta)
+    with pytest.raises(ValueError):
+        plan.eval(p, dev(np.zeros(7)))
+    with pytest.raises(N.GnaError):
+        plan.fit(p.clone(), dev(np.zeros((1, 200))))  # no per-point data rows in this plan
+    with pytest.raises(N.GnaError):
+        plan.tuning = "block=1000"
+    with pytest.raises(N.GnaError):
+        api.Plan([1.0, 2.0], list(range(1, 18)), nodes_per_bin=4)

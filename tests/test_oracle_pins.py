@@ -227,6 +227,39 @@ def test_gl_large_orders(n):
     assert np.all(np.sign(eval_legendre(n, mids[idx])) != np.sign(eval_legendre(n, mids[idx + 1])))
 
 
+def test_gl_edge_weights_mpmath_large_order():
+    """Outermost nodes of the 16384-point rule (1 - x^2 ~ 5e-8).  The node must
+    be the true root rounded to double (Newton in 30-digit arithmetic from the
+    oracle's node), and the weight formula w = 2/((1-x^2) P_n'(x)^2) evaluated at
+    that double node must match 30-digit arithmetic.  (At the true root the
+    weight differs by ~4x/(1-x^2) times the node rounding, ~1e-8 relative.)"""
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = 30
+    n = 16384
+    x, w = oracle.gl(n)
+
+    def leg(t):
+        p0, p1 = mp.mpf(1), t
+        for j in range(1, n):
+            p0, p1 = p1, ((2 * j + 1) * t * p1 - j * p0) / (j + 1)
+        return p1, p0
+
+    def weight(t):
+        pn, pn1 = leg(t)
+        dp = n * (t * pn - pn1) / (t * t - 1)
+        return 2 / ((1 - t * t) * dp * dp)
+
+    for k in (0, 1):
+        t = mp.mpf(x[k])
+        for _ in range(2):
+            pn, pn1 = leg(t)
+            t = t - pn / (n * (t * pn - pn1) / (t * t - 1))
+        assert abs(float(t - mp.mpf(x[k]))) <= 0.5 * np.spacing(abs(x[k]))
+        # the recurrence accumulates ~n rounding errors: bound n * 1e-15
+        assert abs(float(weight(mp.mpf(x[k]))) / w[k] - 1) < n * 1e-15
+
+
 # ---------------------------------------------------- binned prediction ----
 def test_spectrum_closed_form():
     E = np.array([0.5, 1.8, 4.0, 12.0])

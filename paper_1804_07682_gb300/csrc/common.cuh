@@ -33,16 +33,18 @@ struct PointConst {
     double dA12[3];  // d A_ij / d sin^2 theta12
     double dA13[3];  // d A_ij / d sin^2 theta13
     float Af[3], dA12f[3], dA13f[3];
-    float pad[3];
+    float Alo[3];    // A - (double)Af: the amplitudes enter P as hi + lo
 };
 
 // Plan-wide constants passed by value.
 struct BaseConst {
-    float om[GNA_NLMAX];    // omega_r (FP32)
+    float om[GNA_NLMAX];    // omega_r rounded to FP32
+    float omlo[GNA_NLMAX];  // omega_r - om_r (FP32)
     float wkl[GNA_NLMAX];   // 2 omega_r K L_r: d sin^2 D / d dm2 = sin 2D K L / E
     double omd[GNA_NLMAX];  // omega_r (FP64)
     double kld[GNA_NLMAX];  // K L_r (FP64)
-    float wsum;             // sum of the FP32 omegas
+    float wsum;             // sum_r om_r rounded to FP32
+    double wsum_lo;         // sum_r om_r - wsum (exact sum of the FP32 weights)
     int nL;
 };
 

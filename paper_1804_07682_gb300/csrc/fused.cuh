@@ -19,6 +19,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "epilogue.cuh"
 
 namespace gna {
 
@@ -48,10 +49,15 @@ template <int PH, int NL, bool GRAD, bool SPEC>
 struct NodeMath {
     static constexpr int NV = 1 + (GRAD ? 4 : 0) + (SPEC ? NL : 0);
 
+    // With more than one baseline and no per-baseline sums, the weights enter
+    // as hi + lo so that the FP32 rounding of omega_r leaves no bias; with
+    // per-baseline sums the epilogue corrects sum_r (omega_r - om_r) mu_r exactly.
+    static constexpr bool OMLO = (NL > 1) && !SPEC;
+
     PhaseConsts<PH, NL> ph;
-    float om[NL], wkl[NL];
+    float om[NL], omlo[NL], wkl[NL];
     float wsum;
-    float A21, A31, A32;
+    float A21, A31, A32, A21l, A31l, A32l;
     float d12[3], d13[3];
 
     __device__ __forceinline__ void load(const PointConst* pc, const BaseConst& bc) {
@@ -59,12 +65,16 @@ struct NodeMath {
 #pragma unroll
         for (int r = 0; r < NL; r++) {
             om[r] = bc.om[r];
+            omlo[r] = bc.omlo[r];
             wkl[r] = bc.wkl[r];
         }
         wsum = bc.wsum;
         A21 = pc->Af[0];
         A31 = pc->Af[1];
         A32 = pc->Af[2];
+        A21l = pc->Alo[0];
+        A31l = pc->Alo[1];
+        A32l = pc->Alo[2];
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             d12[j] = pc->dA12f[j];
@@ -78,6 +88,7 @@ struct NodeMath {
         double ed = 0.0;
         if (PH == 1) ed = (double)eh + (double)el;
         float U21 = 0.f, U31 = 0.f, U32 = 0.f;
+        float L21 = 0.f, L31 = 0.f, L32 = 0.f;  // lo-weight sums (OMLO)
         float V21 = 0.f, V31 = 0.f, V32 = 0.f;
 #pragma unroll
         for (int r = 0; r < NL; r++) {
@@ -99,6 +110,11 @@ struct NodeMath {
             U21 = fmaf(om[r], S21, U21);
             U31 = fmaf(om[r], S31, U31);
             U32 = fmaf(om[r], S32, U32);
+            if (OMLO) {
+                L21 = fmaf(omlo[r], S21, L21);
+                L31 = fmaf(omlo[r], S31, L31);
+                L32 = fmaf(omlo[r], S32, L32);
+            }
             if (GRAD) {
                 float c3 = fmaf(c1, c2, -(s1 * s2));
                 V21 = fmaf(wkl[r], s1 * c1, V21);
@@ -110,7 +126,11 @@ struct NodeMath {
                 kadd_prod(acc[1 + (GRAD ? 4 : 0) + r], W, Pr);
             }
         }
+        // Pc = wsum - sum_ij (A_ij + A_ij,lo)(U_ij + L_ij): large terms first
         float Pc = fmaf(-A32, U32, fmaf(-A31, U31, fmaf(-A21, U21, wsum)));
+        float Plo = fmaf(-A32l, U32, fmaf(-A31l, U31, -A21l * U21));
+        if (OMLO) Plo = fmaf(-A32, L32, fmaf(-A31, L31, fmaf(-A21, L21, Plo)));
+        Pc = __fadd_rn(Pc, Plo);
         kadd_prod(acc[0], W, Pc);
         if (GRAD) {
             float g12 = fmaf(d12[2], U32, fmaf(d12[1], U31, d12[0] * U21));
@@ -131,15 +151,19 @@ __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v
 // ---------------------------------------------------------------------------
 // Split mapping: a CTA tile is (point p, bin i, node chunk c); the threads
 // stride over the chunk's nodes (bin-major grid: node k of bin i at i*n + k,
-// coalesced 16-byte loads), then the CTA reduces its Kahan sums with a
-// transposed warp-shuffle reduction and shared memory.  Persistent grid:
-// CTAs loop over tiles.
+// coalesced 16-byte loads, the next node prefetched while the current one is
+// computed), then the CTA reduces its Kahan sums with a transposed
+// warp-shuffle reduction and shared memory and stores the chunk's partial.
+// The CTA that stores the last chunk of a bin sums the chunks (double-float,
+// fixed order) and runs the bin epilogue; the last bin of a point to finish
+// reduces the point.  Persistent grid: CTAs loop over tiles.
 struct SplitArgs {
     const float4* grid;
     int nbins, n, chunk, nchunks, npts;
     const PointConst* pcs;
     BaseConst bc;
     float2* part;  // [npts][nbins][nchunks][NV]
+    EpiArgs ea;
 };
 
 template <int PH, int NL, bool GRAD, bool SPEC>
@@ -149,6 +173,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
     constexpr int NVP = pow2ceil(NV);
     constexpr int SH = 5 - ilog2(NVP);
     __shared__ float2 red[8][NVP];
+    __shared__ double sv[NV];
+    __shared__ int s_flag;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
     int last_p = -1;
@@ -168,17 +194,50 @@ __global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
         const int k0 = c * a.chunk;
         const int k1 = min(a.n, k0 + a.chunk);
         const float4* g = a.grid + (int64_t)i * a.n;
-        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) m.update(__ldg(g + k), acc);
+        int k = k0 + threadIdx.x;
+        float4 cur = (k < k1) ? __ldg(g + k) : make_float4(1.f, 0.f, 0.f, 0.f);
+        while (k < k1) {
+            const int kn = k + blockDim.x;
+            const float4 nxt = (kn < k1) ? __ldg(g + kn) : cur;
+            m.update(cur, acc);
+            cur = nxt;
+            k = kn;
+        }
         float2 v[NVP];
 #pragma unroll
         for (int j = 0; j < NVP; j++) v[j] = (j < NV) ? kahan_to_ff(acc[j < NV ? j : 0]) : make_float2(0.f, 0.f);
         warp_transpose_reduce<NVP>(v, lane);
         if ((lane & ((1 << SH) - 1)) == 0) red[warp][lane >> SH] = v[0];
         __syncthreads();
+        float2* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
         if (threadIdx.x < NV) {
             float2 s = red[0][threadIdx.x];
             for (int w = 1; w < nwarps; w++) s = ff_add(s, red[w][threadIdx.x]);
-            a.part[(((int64_t)p * a.nbins + i) * a.nchunks + c) * NV + threadIdx.x] = s;
+            pp[c * NV + threadIdx.x] = s;
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_flag = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
+        __syncthreads();
+        if (s_flag) {
+            // last chunk of bin (p, i): sum the chunks in order and finish the bin
+            __threadfence();
+            if (threadIdx.x < NV) {
+                float2 s = __ldcg(pp + threadIdx.x);
+                for (int cc = 1; cc < a.nchunks; cc++) s = ff_add(s, __ldcg(pp + cc * NV + threadIdx.x));
+                sv[threadIdx.x] = (double)s.x + (double)s.y;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bin_epilogue(a.ea, p, i, sv);
+                __threadfence();
+                s_flag = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                point_reduce(a.ea, p, warp, nwarps, lane);
+            }
         }
         __syncthreads();
     }
@@ -187,7 +246,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
 // ---------------------------------------------------------------------------
 // Bin mapping: a warp task is (point p, group b of 32 consecutive bins); lane
 // l owns bin 32 b + l and walks all its nodes (grid layout [group][k][lane],
-// so each warp load is 512 contiguous bytes).  No cross-thread reduction.
+// so each warp load is 512 contiguous bytes, the next one prefetched).  Each
+// lane finishes its own bin; the last warp of a point reduces the point.
 // Warps take tasks from a global counter; tasks are ordered by decreasing
 // node count so that uneven grids balance.
 struct BinArgs {
@@ -199,8 +259,8 @@ struct BinArgs {
     int ntasks, ngroups, nbins;
     const PointConst* pcs;
     BaseConst bc;
-    float2* part;  // [npts][nbins][NV]
     int* counter;  // zeroed before the launch
+    EpiArgs ea;
 };
 
 template <int PH, int NL, bool GRAD, bool SPEC>
@@ -228,12 +288,27 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
 #pragma unroll
         for (int v = 0; v < NV; v++) kzero(acc[v]);
         const float4* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
-        for (int k = 0; k < n; k++) m.update(__ldg(g + (int64_t)k * 32), acc);
+        float4 cur = __ldg(g);
+        for (int k = 0; k < n; k++) {
+            const float4 nxt = (k + 1 < n) ? __ldg(g + (int64_t)(k + 1) * 32) : cur;
+            m.update(cur, acc);
+            cur = nxt;
+        }
         const int i = b * 32 + lane;
         if (i < a.nbins) {
-            float2* o = a.part + ((int64_t)p * a.nbins + i) * NV;
+            double v[NV];
 #pragma unroll
-            for (int v = 0; v < NV; v++) o[v] = kahan_to_ff(acc[v]);
+            for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
+            bin_epilogue(a.ea, p, i, v);
+            __threadfence();
+        }
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = (atomicAdd(a.ea.pt_cnt + p, 1) == a.ngroups - 1);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            point_reduce(a.ea, p, 0, 1, lane);
         }
     }
 }

@@ -72,6 +72,7 @@ struct SplitArgs64 {
     const PointConst* pcs;
     BaseConst bc;
     double* part;  // [npts][nbins][nchunks][NV]
+    EpiArgs ea;
 };
 
 template <int NL, bool GRAD, bool SPEC>
@@ -79,6 +80,8 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
     using M = NodeMath64<NL, GRAD, SPEC>;
     constexpr int NV = M::NV;
     __shared__ double red[8][NV];
+    __shared__ double sv[NV];
+    __shared__ int s_flag;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
     int last_p = -1;
@@ -107,10 +110,34 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
             if (lane == 0) red[warp][v] = x;
         }
         __syncthreads();
+        double* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
         if (threadIdx.x < NV) {
             double s = red[0][threadIdx.x];
             for (int w = 1; w < nwarps; w++) s += red[w][threadIdx.x];
-            a.part[(((int64_t)p * a.nbins + i) * a.nchunks + c) * NV + threadIdx.x] = s;
+            pp[c * NV + threadIdx.x] = s;
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_flag = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
+        __syncthreads();
+        if (s_flag) {
+            __threadfence();
+            if (threadIdx.x < NV) {
+                double s = __ldcg(pp + threadIdx.x);
+                for (int cc = 1; cc < a.nchunks; cc++) s += __ldcg(pp + cc * NV + threadIdx.x);
+                sv[threadIdx.x] = s;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bin_epilogue(a.ea, p, i, sv);
+                __threadfence();
+                s_flag = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                point_reduce(a.ea, p, warp, nwarps, lane);
+            }
         }
         __syncthreads();
     }
@@ -125,8 +152,8 @@ struct BinArgs64 {
     int ntasks, ngroups, nbins;
     const PointConst* pcs;
     BaseConst bc;
-    double* part;  // [npts][nbins][NV]
     int* counter;
+    EpiArgs ea;
 };
 
 template <int NL, bool GRAD, bool SPEC>
@@ -157,9 +184,16 @@ __global__ void __launch_bounds__(256) k_fused64_bins(BinArgs64 a) {
         for (int k = 0; k < n; k++) m.update(g[(int64_t)k * 32], acc);
         const int i = b * 32 + lane;
         if (i < a.nbins) {
-            double* o = a.part + ((int64_t)p * a.nbins + i) * NV;
-#pragma unroll
-            for (int v = 0; v < NV; v++) o[v] = acc[v];
+            bin_epilogue(a.ea, p, i, acc);
+            __threadfence();
+        }
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = (atomicAdd(a.ea.pt_cnt + p, 1) == a.ngroups - 1);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            point_reduce(a.ea, p, 0, 1, lane);
         }
     }
 }

@@ -98,7 +98,8 @@ struct gna_plan {
     int ngrids = 0, ngroups = 0;
     int* d_tasks = nullptr;
     int ntasks = 0;
-    int* d_counter = nullptr;
+    int* d_counters = nullptr;  // [1 + npts + npts*nbins (split)]: work counter, per-point, per-bin arrivals
+    int64_t ncounters = 0;
     double* d_edges = nullptr;
     // constants
     BaseConst bc{};
@@ -143,6 +144,11 @@ struct gna_plan {
     std::vector<cudaEvent_t> prof_ev;  // pairs
     int prof_n = 0;
     double* d_spec_stage = nullptr;
+    double* d_sumW = nullptr;  // [ngrids][nbins]
+    double wsum_all_lo = 0.0;  // sum_r (om_r + omlo_r) - wsum: constant term when the weights enter as hi + lo
+    // graphs are captured on a plan-owned stream joined to the caller's by events
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -159,10 +165,13 @@ gna_status fail(gna_plan* p, gna_status s, const char* fmt, ...) {
     return s;
 }
 
-#define CU(call)                                                                                           \
-    do {                                                                                                   \
-        cudaError_t e_ = (call);                                                                           \
-        if (e_ != cudaSuccess) return fail(plan, GNA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+#define CU(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            cudaGetLastError(); /* consume the (non-sticky) error so later calls start clean */       \
+            return fail(plan, GNA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                    \
+        }                                                                                             \
     } while (0)
 
 template <typename T>
@@ -234,52 +243,17 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     const bool grad = q.grad || q.grad_eta || q.H;
     const bool spec = q.spectra != nullptr;
     int nl = 0;
-    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s));
-    nl++;
     const int NV = value_count(plan, grad, spec);
     const int nchunks = nchunks_of(plan);
-    if ((size_t)plan->npts * plan->nbins * nchunks * NV > plan->part_cap)
+    if (plan->mapping == MAP_SPLIT && (size_t)plan->npts * plan->nbins * nchunks * NV > plan->part_cap)
         return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
                     (long long)plan->npts * plan->nbins * nchunks * NV, plan->part_cap);
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cap);
-    const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
-    if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
-    if (plan->mapping == MAP_SPLIT) {
-        const int64_t tiles = (int64_t)plan->npts * plan->nbins * nchunks;
-        const int g = grid_size(plan, grad, spec, tiles);
-        if (plan->ph < 2) {
-            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
-                        plan->d_pc, plan->bc, (float2*)plan->d_part};
-            CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
-        } else {
-            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
-                          plan->d_pc, plan->bc, (double*)plan->d_part};
-            CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
-        }
-        nl++;
-    } else {
-        CU(cudaMemsetAsync(plan->d_counter, 0, sizeof(int), s));
-        const int g = grid_size(plan, grad, spec, plan->ntasks);
-        if (plan->ph < 2) {
-            BinArgs a{plan->grid_ff, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
-                      plan->ngroups, plan->nbins, plan->d_pc, plan->bc, (float2*)plan->d_part, plan->d_counter};
-            CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
-        } else {
-            BinArgs64 a{plan->grid64, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
-                        plan->ngroups, plan->nbins, plan->d_pc, plan->bc, (double*)plan->d_part, plan->d_counter};
-            CU(dispatch_bins(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
-        }
-        nl++;
-    }
-    if (timed) {
-        CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n + 1], s));
-        plan->prof_n++;
-    }
+    // work counter, per-point and per-bin arrival counters: one memset
+    CU(cudaMemsetAsync(plan->d_counters, 0, sizeof(int) * plan->ncounters, s));
+    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s));
+    nl++;
     EpiArgs ea{};
-    ea.part = plan->d_part;
     ea.is64 = plan->ph == 2;
-    ea.nchunks = nchunks;
     ea.NV = NV;
     ea.has_grad = grad;
     ea.nspec = spec ? plan->nl_inst : 0;
@@ -297,8 +271,51 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     ea.grad_eta_out = q.grad_eta;
     ea.binvals = plan->d_binvals;
     ea.NBV = q.H ? 15 : (grad ? 5 : 1);
-    CU(launch_epilogue(ea, q.chi2, q.grad, q.H, s));
-    nl += 2;
+    ea.sumW = plan->d_sumW;
+    ea.shared_grid = plan->ngrids == 1;
+    // the kernel's constant term is wsum; the exact one is sum_r om_r when the
+    // per-baseline sums carry the weight correction (or one baseline), else
+    // sum_r (om_r + omlo_r)
+    ea.wsum_lo = (spec || plan->nl_inst == 1) ? plan->bc.wsum_lo : plan->wsum_all_lo;
+    for (int r = 0; r < GNA_NLMAX; r++) ea.om_delta[r] = (r < plan->nL) ? plan->bc.omd[r] - (double)plan->bc.om[r] : 0.0;
+    ea.chi2 = q.chi2;
+    ea.grad = q.grad;
+    ea.H = q.H;
+    ea.pt_cnt = plan->d_counters + 1;
+    ea.bin_cnt = plan->d_counters + 1 + plan->npts;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cap));
+    const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
+    if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
+    if (plan->mapping == MAP_SPLIT) {
+        const int64_t tiles = (int64_t)plan->npts * plan->nbins * nchunks;
+        const int g = grid_size(plan, grad, spec, tiles);
+        if (plan->ph < 2) {
+            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
+                        plan->d_pc, plan->bc, (float2*)plan->d_part, ea};
+            CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        } else {
+            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
+                          plan->d_pc, plan->bc, (double*)plan->d_part, ea};
+            CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        }
+    } else {
+        const int g = grid_size(plan, grad, spec, plan->ntasks);
+        if (plan->ph < 2) {
+            BinArgs a{plan->grid_ff, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+                      plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea};
+            CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        } else {
+            BinArgs64 a{plan->grid64, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+                        plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea};
+            CU(dispatch_bins(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        }
+    }
+    nl++;
+    if (timed) {
+        CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n + 1], s));
+        plan->prof_n++;
+    }
     *launches = nl;
     return GNA_OK;
 }
@@ -389,6 +406,9 @@ gna_status gna_plan_destroy(gna_plan* plan) {
     if (!plan) return GNA_OK;
     destroy_graph(plan);
     destroy_profile(plan);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    if (plan->ev_in) cudaEventDestroy(plan->ev_in);
+    if (plan->ev_out) cudaEventDestroy(plan->ev_out);
     for (void* v : plan->allocs) cudaFree(v);
     delete plan;
     return GNA_OK;
@@ -445,10 +465,15 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         bc.omd[r] = plan->omega[r];
         bc.kld[r] = GNA_K_PHASE * d->L[r];
         bc.om[r] = (float)plan->omega[r];
+        bc.omlo[r] = (float)(plan->omega[r] - (double)bc.om[r]);
         bc.wkl[r] = (float)(2.0 * plan->omega[r] * bc.kld[r]);
-        fsum += (double)bc.om[r];
+        fsum += (double)bc.om[r];  // exact: a handful of floats summed in double
     }
     bc.wsum = (float)fsum;
+    bc.wsum_lo = fsum - (double)bc.wsum;
+    double fall = 0.0;
+    for (int r = 0; r < d->nL; r++) fall += (double)bc.om[r] + (double)bc.omlo[r];
+    plan->wsum_all_lo = fall - (double)bc.wsum;
     // mapping
     const int ngroups = (d->nbins + 31) / 32;
     plan->ngroups = ngroups;
@@ -513,6 +538,14 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
                              plan->grid64 ? plan->grid64 + goff[g] : nullptr, (g == 0) ? plan->plain64 : nullptr, s));
     }
     if (plain_alias) plan->plain64 = plan->grid64;
+    if (plan->grid_ff) {
+        TRY(dalloc(plan, &plan->d_sumW, (size_t)plan->ngrids * d->nbins));
+        for (int g = 0; g < plan->ngrids; g++)
+            CU(launch_sum_weights(plan->grid_ff + goff[g], d->nbins, gn[g], layout, plan->d_sumW + (size_t)g * d->nbins, s));
+    }
+    CU(cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&plan->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&plan->ev_out, cudaEventDisableTiming));
     // task list (bins mapping): (point, group) ordered by decreasing node count
     if (plan->mapping == MAP_BINS) {
         if ((int64_t)d->npts * ngroups >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many bin groups");
@@ -526,15 +559,17 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         plan->ntasks = (int)tasks.size();
         TRY(dalloc(plan, &plan->d_tasks, tasks.size()));
         CU(cudaMemcpyAsync(plan->d_tasks, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, s));
-        TRY(dalloc(plan, &plan->d_counter, 1));
     }
+    plan->ncounters = 1 + (int64_t)d->npts + (plan->mapping == MAP_SPLIT ? (int64_t)d->npts * d->nbins : 0);
+    TRY(dalloc(plan, &plan->d_counters, plan->ncounters));
     // scratch
     TRY(dalloc(plan, &plan->d_pc, d->npts));
     const int nv_max = fused_nv(plan->nl_inst, true, true);
-    int max_chunks = 1;
-    if (plan->mapping == MAP_SPLIT) max_chunks = (plan->n_uniform + 64 * 4 - 1) / (64 * 4);  // smallest tile: 64 x 4
-    plan->part_cap = (size_t)d->npts * d->nbins * max_chunks * nv_max;
-    TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
+    if (plan->mapping == MAP_SPLIT) {
+        const int max_chunks = (plan->n_uniform + 64 * 4 - 1) / (64 * 4);  // smallest tile: 64 x 4
+        plan->part_cap = (size_t)d->npts * d->nbins * max_chunks * nv_max;
+        TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
+    }
     TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
     TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
     TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
@@ -620,28 +655,36 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
     GraphKey key{{(uintptr_t)params, (uintptr_t)eta, sigbits, (uintptr_t)data, (uintptr_t)data_per_point,
                   (uintptr_t)out->chi2, (uintptr_t)out->grad, (uintptr_t)out->grad_eta, (uintptr_t)out->mu,
                   (uintptr_t)out->spectra, (uintptr_t)plan->block, (uintptr_t)plan->npt, (uintptr_t)plan->grid_mult}};
+    cudaStream_t cs = plan->cap_stream;
     if (!plan->gexec || !(key == plan->gkey)) {
         destroy_graph(plan);
-        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         int nl = 0;
-        gna_status st = enqueue_eval(plan, q, s, &nl);
+        gna_status st = enqueue_eval(plan, q, cs, &nl);
         cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(s, &g);
-        if (st != GNA_OK) {
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (st != GNA_OK || e != cudaSuccess) {
+            cudaGetLastError();
             if (g) cudaGraphDestroy(g);
-            return st;
+            if (st != GNA_OK) return st;
+            return fail(plan, GNA_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         }
-        if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&plan->gexec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
+            cudaGetLastError();
             plan->gexec = nullptr;
             return fail(plan, GNA_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
         }
         plan->gkey = key;
         plan->graph_launches = nl;
     }
-    CU(cudaGraphLaunch(plan->gexec, s));
+    // join the caller's stream: caller -> plan stream -> graph -> caller
+    CU(cudaEventRecord(plan->ev_in, s));
+    CU(cudaStreamWaitEvent(cs, plan->ev_in, 0));
+    CU(cudaGraphLaunch(plan->gexec, cs));
+    CU(cudaEventRecord(plan->ev_out, cs));
+    CU(cudaStreamWaitEvent(s, plan->ev_out, 0));
     plan->last_launches = plan->graph_launches;
     return GNA_OK;
 }
@@ -718,31 +761,37 @@ gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, in
     EvalReq q{params, nullptr, 0.0, data, 1, plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr, plan->d_H};
     int launches = 1;
     if (use_graph) {
+        cudaStream_t cs = plan->cap_stream;
         cudaGraph_t g = nullptr;
-        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         int nl = 0;
-        gna_status st = enqueue_eval(plan, q, s, &nl);
+        gna_status st = enqueue_eval(plan, q, cs, &nl);
         cudaError_t e1 = launch_lm_update(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, plan->d_lm, params,
-                                          chi2_out, s);
-        cudaError_t e = cudaStreamEndCapture(s, &g);
-        if (st != GNA_OK) {
+                                          chi2_out, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (st != GNA_OK || e1 != cudaSuccess || e != cudaSuccess) {
+            cudaGetLastError();
             if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        if (e1 != cudaSuccess || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
+            if (st != GNA_OK) return st;
             return fail(plan, GNA_ECUDA, "fit graph capture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e));
         }
         cudaGraphExec_t ex = nullptr;
         e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "fit graph instantiate: %s", cudaGetErrorString(e));
-        for (int it = 0; it < iters; it++) {
-            e = cudaGraphLaunch(ex, s);
-            if (e != cudaSuccess) break;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(plan, GNA_ECUDA, "fit graph instantiate: %s", cudaGetErrorString(e));
         }
+        CU(cudaEventRecord(plan->ev_in, s));
+        CU(cudaStreamWaitEvent(cs, plan->ev_in, 0));
+        for (int it = 0; it < iters && e == cudaSuccess; it++) e = cudaGraphLaunch(ex, cs);
+        cudaError_t e2 = cudaEventRecord(plan->ev_out, cs);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, plan->ev_out, 0);
         cudaGraphExecDestroy(ex);
-        if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "fit graph launch: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            cudaGetLastError();
+            return fail(plan, GNA_ECUDA, "fit graph launch: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
         launches += iters * (nl + 1);
     } else {
         for (int it = 0; it < iters; it++) {

@@ -14,44 +14,48 @@ namespace gna {
 // --------------------------------------------------------------- step a0 --
 // |U_e1|^2 = (1-s12)(1-s13), |U_e2|^2 = s12 (1-s13), |U_e3|^2 = s13 give
 // A21 = 4 s12 (1-s12)(1-s13)^2, A31 = 4 (1-s12)(1-s13) s13, A32 = 4 s12 (1-s13) s13
-// and their derivatives with respect to s12 = sin^2 theta12, s13 = sin^2 theta13.
-__device__ void prepare_point(const gna_osc& o, const BaseConst& bc, PointConst& pc) {
-    const double s12 = o.s2_12, s13 = o.s2_13;
-    const double c12 = 1.0 - s12, c13 = 1.0 - s13;
-    pc.A[0] = 4.0 * s12 * c12 * c13 * c13;
-    pc.A[1] = 4.0 * c12 * c13 * s13;
-    pc.A[2] = 4.0 * s12 * c13 * s13;
-    pc.dA12[0] = 4.0 * (1.0 - 2.0 * s12) * c13 * c13;
-    pc.dA12[1] = -4.0 * c13 * s13;
-    pc.dA12[2] = 4.0 * c13 * s13;
-    pc.dA13[0] = -8.0 * s12 * c12 * c13;
-    pc.dA13[1] = 4.0 * c12 * (1.0 - 2.0 * s13);
-    pc.dA13[2] = 4.0 * s12 * (1.0 - 2.0 * s13);
-    for (int j = 0; j < 3; j++) {
-        pc.Af[j] = (float)pc.A[j];
-        pc.dA12f[j] = (float)pc.dA12[j];
-        pc.dA13f[j] = (float)pc.dA13[j];
-    }
-    for (int r = 0; r < GNA_NLMAX; r++) {
-        const double kl = (r < bc.nL) ? bc.kld[r] : 0.0;
-        pc.c21[r] = o.dm2_21 * kl;
-        pc.c32[r] = o.dm2_32 * kl;
-        split_ff(pc.c21[r], pc.c21h[r], pc.c21l[r]);
-        split_ff(pc.c32[r], pc.c32h[r], pc.c32l[r]);
-    }
-    pc.pad[0] = pc.pad[1] = pc.pad[2] = 0.f;
-}
-
+// and their derivatives with respect to s12 = sin^2 theta12, s13 = sin^2 theta13;
+// the phase constants are c_ij,r = K dm2_ij L_r.  One thread per (point, baseline slot).
 __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, BaseConst bc, PointConst* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = idx / GNA_NLMAX, r = idx % GNA_NLMAX;
     if (p >= npts) return;
-    PointConst pc;
-    prepare_point(prm[p], bc, pc);
-    out[p] = pc;
+    const gna_osc o = prm[p];
+    PointConst& pc = out[p];
+    const double kl = (r < bc.nL) ? bc.kld[r] : 0.0;
+    const double c21 = o.dm2_21 * kl, c32 = o.dm2_32 * kl;
+    pc.c21[r] = c21;
+    pc.c32[r] = c32;
+    split_ff(c21, pc.c21h[r], pc.c21l[r]);
+    split_ff(c32, pc.c32h[r], pc.c32l[r]);
+    if (r == 0) {
+        const double s12 = o.s2_12, s13 = o.s2_13;
+        const double c12 = 1.0 - s12, c13 = 1.0 - s13;
+        double A[3], d12[3], d13[3];
+        A[0] = 4.0 * s12 * c12 * c13 * c13;
+        A[1] = 4.0 * c12 * c13 * s13;
+        A[2] = 4.0 * s12 * c13 * s13;
+        d12[0] = 4.0 * (1.0 - 2.0 * s12) * c13 * c13;
+        d12[1] = -4.0 * c13 * s13;
+        d12[2] = 4.0 * c13 * s13;
+        d13[0] = -8.0 * s12 * c12 * c13;
+        d13[1] = 4.0 * c12 * (1.0 - 2.0 * s13);
+        d13[2] = 4.0 * s12 * (1.0 - 2.0 * s13);
+        for (int j = 0; j < 3; j++) {
+            pc.A[j] = A[j];
+            pc.dA12[j] = d12[j];
+            pc.dA13[j] = d13[j];
+            pc.Af[j] = (float)A[j];
+            pc.Alo[j] = (float)(A[j] - (double)(float)A[j]);
+            pc.dA12f[j] = (float)d12[j];
+            pc.dA13f[j] = (float)d13[j];
+        }
+    }
 }
 
 cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s) {
-    k_prepare_points<<<(npts + 127) / 128, 128, 0, s>>>(prm, npts, bc, out);
+    const int64_t threads = (int64_t)npts * GNA_NLMAX;
+    k_prepare_points<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, out);
     return cudaGetLastError();
 }
 
@@ -146,111 +150,29 @@ __global__ void k_build_grid(int nbins, int nbins_pad, const double* __restrict_
     if (plain64 && i < nbins) plain64[idx] = make_double2(invE, Wd);
 }
 
+// Sum of the FP32 node weights of each bin, in double (for the epilogue's
+// exact correction of the constant term).
+__global__ void k_sum_weights(const float4* __restrict__ grid, int nbins, int n, int layout, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbins) return;
+    double s = 0.0;
+    for (int k = 0; k < n; k++) {
+        const int64_t pos = (layout == 0) ? (int64_t)i * n + k : (((int64_t)(i >> 5) * n + k) * 32 + (i & 31));
+        s += (double)grid[pos].z;
+    }
+    out[i] = s;
+}
+
+cudaError_t launch_sum_weights(const float4* grid, int nbins, int n, int layout, double* out, cudaStream_t s) {
+    k_sum_weights<<<(nbins + 127) / 128, 128, 0, s>>>(grid, nbins, n, layout, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int n, const double* x, const double* w,
                               double e_scale, int layout, float4* ff, double2* d64, double2* plain64, cudaStream_t s) {
     const int64_t total = (int64_t)nbins_pad * n;
     const int64_t blocks = (total + 255) / 256;
     k_build_grid<<<(unsigned)blocks, 256, 0, s>>>(nbins, nbins_pad, edges, n, x, w, e_scale, layout, ff, d64, plain64);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------ steps a7-a9 --
-// Per (point, bin): sum the node-chunk partials, form
-//   M_i = sum_r omega_r mu_r,i,  mu_i = N (1 + eta_i) M_i,
-//   Pearson chi2_i = (d - mu)^2 / mu,  g_i = 1 - d^2 / mu^2,
-//   Poisson chi2_i = 2 (mu - d + d ln(d/mu)) (2 mu if d = 0), g_i = 2 (1 - d/mu),
-// plus eta_i^2 / sigma^2, the gradient terms g_i N (1+eta_i) dM_i/dtheta and,
-// for the fitter, (2 / mu_i) J_i J_i^T with J_i = N (1+eta_i) dM_i/dtheta.
-__global__ void k_epi_bin(EpiArgs a) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)a.npts * a.nbins) return;
-    const int p = (int)(idx / a.nbins);
-    const int i = (int)(idx - (int64_t)p * a.nbins);
-    double v[GNA_NV_BASE + GNA_NLMAX];
-    for (int j = 0; j < a.NV; j++) v[j] = 0.0;
-    if (a.is64) {
-        const double* src = (const double*)a.part + idx * a.nchunks * a.NV;
-        for (int c = 0; c < a.nchunks; c++)
-            for (int j = 0; j < a.NV; j++) v[j] += src[c * a.NV + j];
-    } else {
-        const float2* src = (const float2*)a.part + idx * a.nchunks * a.NV;
-        for (int c = 0; c < a.nchunks; c++)
-            for (int j = 0; j < a.NV; j++) {
-                const float2 f = src[c * a.NV + j];
-                v[j] += (double)f.x + (double)f.y;
-            }
-    }
-    const double M = v[0];
-    const double e = a.eta ? a.eta[i] : 0.0;
-    const double f = a.norm * (1.0 + e);
-    const double mu = f * M;
-    const double d = a.data[a.data_per_point ? idx : i];
-    double term, g;
-    if (a.kind == GNA_PEARSON) {
-        term = (d - mu) * (d - mu) / mu;
-        g = 1.0 - (d * d) / (mu * mu);
-    } else {
-        term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
-        g = 2.0 * (1.0 - d / mu);
-    }
-    const bool pen = a.eta && a.sigma > 0.0;
-    if (pen) term += e * e / (a.sigma * a.sigma);
-    double* bv = a.binvals + idx * a.NBV;
-    bv[0] = term;
-    if (a.has_grad && a.NBV >= 5) {
-        double J[4];
-        for (int q = 0; q < 4; q++) {
-            J[q] = -f * v[1 + q];
-            bv[1 + q] = g * J[q];
-        }
-        if (a.NBV >= 15) {
-            const double h = 2.0 / mu;
-            int t = 5;
-            for (int q = 0; q < 4; q++)
-                for (int r = q; r < 4; r++) bv[t++] = h * J[q] * J[r];
-        }
-    }
-    if (a.mu_out) a.mu_out[idx] = mu;
-    if (a.grad_eta_out) a.grad_eta_out[idx] = g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
-    if (a.spectra_out && a.nspec > 0) {
-        const int off = 1 + (a.has_grad ? 4 : 0);
-        for (int r = 0; r < a.nL_out; r++) a.spectra_out[((int64_t)p * a.nL_out + r) * a.nbins + i] = v[off + r];
-    }
-}
-
-// Per point: fixed-order tree sum over bins of the per-bin values.
-__global__ void k_epi_point(const double* __restrict__ binvals, int nbins, int NBV, double* __restrict__ chi2,
-                            double* __restrict__ grad, double* __restrict__ H) {
-    __shared__ double sh[256];
-    const int p = blockIdx.x;
-    const double* bv = binvals + (int64_t)p * nbins * NBV;
-    for (int v = 0; v < NBV; v++) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nbins; i += blockDim.x) s += bv[(int64_t)i * NBV + v];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const double tot = sh[0];
-            if (v == 0) {
-                if (chi2) chi2[p] = tot;
-            } else if (v < 5) {
-                if (grad) grad[(int64_t)p * 4 + v - 1] = tot;
-            } else if (H) {
-                H[(int64_t)p * 10 + v - 5] = tot;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-cudaError_t launch_epilogue(const EpiArgs& a, double* chi2, double* grad, double* H, cudaStream_t s) {
-    const int64_t total = (int64_t)a.npts * a.nbins;
-    k_epi_bin<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(a);
-    k_epi_point<<<a.npts, 256, 0, s>>>(a.binvals, a.nbins, a.NBV, chi2, grad, H);
     return cudaGetLastError();
 }
 

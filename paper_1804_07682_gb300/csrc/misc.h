@@ -5,27 +5,10 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "epilogue.cuh"
 #include "gnaosc.h"
 
 namespace gna {
-
-struct EpiArgs {
-    const void* part;  // float2 (mixed) or double (FP64) [npts][nbins][nchunks][NV]
-    int is64;
-    int nchunks, NV, has_grad, nspec, nL_out;
-    int npts, nbins;
-    double norm;
-    int kind;
-    const double* eta;
-    double sigma;
-    const double* data;
-    int data_per_point;
-    double* mu_out;
-    double* spectra_out;
-    double* grad_eta_out;
-    double* binvals;  // [npts][nbins][NBV]
-    int NBV;          // 1 (chi2), 5 (+ gradient), 15 (+ J^T W J)
-};
 
 struct PlainChi2Args {
     const double* mu_r;  // [nL][nbins]
@@ -65,7 +48,7 @@ cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, Po
 cudaError_t launch_gl(int n, double* x, double* w, double* tmp_ab, cudaStream_t s);
 cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int n, const double* x, const double* w,
                               double e_scale, int layout, float4* ff, double2* d64, double2* plain64, cudaStream_t s);
-cudaError_t launch_epilogue(const EpiArgs& a, double* chi2, double* grad, double* H, cudaStream_t s);
+cudaError_t launch_sum_weights(const float4* grid, int nbins, int n, int layout, double* out, cudaStream_t s);
 cudaError_t launch_plain_point(const double2* nodes, int nbins, int n, const PointConst* pc, const BaseConst& bc, int nL,
                                int grad, double* P, double* dP, double* mu_r, double* dmu, const PlainChi2Args& ca,
                                cudaStream_t s);

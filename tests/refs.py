@@ -47,3 +47,13 @@ def normrel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def chi2_err_bound(ref, data, kind):
+    """Scale of chi^2 errors implied by relative errors in mu: |d chi2| <=
+    eps * sum_i |d chi2 / d mu_i| mu_i, so a 1e-6 gate on mu carries over to
+    chi^2 as 1e-6 * max(chi2, sum_i |g_i| mu_i)."""
+    mu = np.asarray(ref["mu"], dtype=np.float64)
+    d = np.asarray(data, dtype=np.float64)
+    g = (1 - d * d / (mu * mu)) if kind == 0 else 2 * (1 - d / mu)
+    return max(abs(ref["chi2"]), float(np.sum(np.abs(g) * mu)))

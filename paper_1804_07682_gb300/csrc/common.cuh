@@ -122,8 +122,7 @@ __device__ __forceinline__ void sincos_poly(float r, float& s, float& c) {
     ps = fmaf(ps, u, GNA_SIN_C2);
     ps = fmaf(ps, u, GNA_SIN_C1);
     s = fmaf(__fmul_rn(r, u), ps, r);
-    float pc = fmaf(GNA_COS_C6, u, GNA_COS_C5);
-    pc = fmaf(pc, u, GNA_COS_C4);
+    float pc = fmaf(GNA_COS_C5, u, GNA_COS_C4);
     pc = fmaf(pc, u, GNA_COS_C3);
     pc = fmaf(pc, u, GNA_COS_C2);
     pc = fmaf(pc, u, GNA_COS_C1);

@@ -19,7 +19,7 @@ import numpy as np
 
 R_MAX = math.pi / 2 + 2e-3
 N_SIN = 5  # S1..S5: odd degree 11
-N_COS = 6  # C1..C6: even degree 12
+N_COS = 5  # C1..C5: even degree 10
 
 # pi to 60 digits (textbook value)
 PI = Fraction("3.14159265358979323846264338327950288419716939937510582097494")

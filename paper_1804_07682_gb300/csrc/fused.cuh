@@ -92,6 +92,7 @@ struct NodeMath {
         float V21 = 0.f, V31 = 0.f, V32 = 0.f;
 #pragma unroll
         for (int r = 0; r < NL; r++) {
+            float s1, c1, s2, c2;
             float r21, r32;
             if (PH == 0) {
                 r21 = reduce_pi_ff(ph.ch21[r], ph.cl21[r], eh, el);
@@ -100,7 +101,6 @@ struct NodeMath {
                 r21 = reduce_pi_f64(ph.cd21[r], ed);
                 r32 = reduce_pi_f64(ph.cd32[r], ed);
             }
-            float s1, c1, s2, c2;
             sincos_poly(r21, s1, c1);
             sincos_poly(r32, s2, c2);
             // D31 = D21 + D32 (up to a multiple of pi, which flips a common sign
@@ -149,39 +149,45 @@ __host__ __device__ constexpr int pow2ceil(int v) { return v <= 1 ? 1 : v <= 2 ?
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
 // ---------------------------------------------------------------------------
-// Split mapping: a CTA tile is (point p, bin i, node chunk c); the threads
-// stride over the chunk's nodes (bin-major grid: node k of bin i at i*n + k,
-// coalesced 16-byte loads, the next node prefetched while the current one is
-// computed), then the CTA reduces its Kahan sums with a transposed
-// warp-shuffle reduction and shared memory and stores the chunk's partial.
-// The CTA that stores the last chunk of a bin sums the chunks (double-float,
-// fixed order) and runs the bin epilogue; the last bin of a point to finish
-// reduces the point.  Persistent grid: CTAs loop over tiles.
+// Split mapping: a warp tile is (point p, bin i, node chunk c of 32 m nodes);
+// lane l takes nodes c 32 m + l + 32 j (bin-major grid, node k of bin i at
+// i n + k: every warp load is 512 contiguous bytes, the next one prefetched
+// while the current node is computed), then the warp reduces its Kahan sums
+// with a transposed shuffle reduction and stores the chunk's partial.  Warps
+// take tiles from a global counter (no CTA barriers anywhere).  The warp that
+// stores the last chunk of a bin sums the chunks in order (double-float) and
+// runs the bin epilogue; the last bin of a point to finish reduces the point.
 struct SplitArgs {
     const float4* grid;
     int nbins, n, chunk, nchunks, npts;
     const PointConst* pcs;
     BaseConst bc;
-    float2* part;  // [npts][nbins][nchunks][NV]
+    float2* part;   // [npts][nbins][nchunks][NV]
+    int* counter;   // tile counter, zeroed before the launch
     EpiArgs ea;
 };
 
+#ifndef GNA_SPLIT_MIN_BLOCKS
+#define GNA_SPLIT_MIN_BLOCKS 2
+#endif
+
 template <int PH, int NL, bool GRAD, bool SPEC>
-__global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
+__global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(SplitArgs a) {
     using M = NodeMath<PH, NL, GRAD, SPEC>;
     constexpr int NV = M::NV;
     constexpr int NVP = pow2ceil(NV);
     constexpr int SH = 5 - ilog2(NVP);
-    __shared__ float2 red[8][NVP];
-    __shared__ double sv[NV];
-    __shared__ int s_flag;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
     int last_p = -1;
     M m;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int c = (int)(tile % a.nchunks);
-        const int64_t t2 = tile / a.nchunks;
+    while (true) {
+        int64_t t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int c = (int)(t % a.nchunks);
+        const int64_t t2 = t / a.nchunks;
         const int i = (int)(t2 % a.nbins);
         const int p = (int)(t2 / a.nbins);
         if (p != last_p) {
@@ -191,13 +197,12 @@ __global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
         KahanF acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) kzero(acc[v]);
-        const int k0 = c * a.chunk;
-        const int k1 = min(a.n, k0 + a.chunk);
+        const int k1 = min(a.n, (c + 1) * a.chunk);
         const float4* g = a.grid + (int64_t)i * a.n;
-        int k = k0 + threadIdx.x;
+        int k = c * a.chunk + lane;
         float4 cur = (k < k1) ? __ldg(g + k) : make_float4(1.f, 0.f, 0.f, 0.f);
         while (k < k1) {
-            const int kn = k + blockDim.x;
+            const int kn = k + 32;
             const float4 nxt = (kn < k1) ? __ldg(g + kn) : cur;
             m.update(cur, acc);
             cur = nxt;
@@ -207,39 +212,41 @@ __global__ void __launch_bounds__(256, 2) k_fused_split(SplitArgs a) {
 #pragma unroll
         for (int j = 0; j < NVP; j++) v[j] = (j < NV) ? kahan_to_ff(acc[j < NV ? j : 0]) : make_float2(0.f, 0.f);
         warp_transpose_reduce<NVP>(v, lane);
-        if ((lane & ((1 << SH) - 1)) == 0) red[warp][lane >> SH] = v[0];
-        __syncthreads();
+        // lane l holds value (l >> SH); lanes with (l mod 2^SH) == 0 store it
         float2* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
-        if (threadIdx.x < NV) {
-            float2 s = red[0][threadIdx.x];
-            for (int w = 1; w < nwarps; w++) s = ff_add(s, red[w][threadIdx.x]);
-            pp[c * NV + threadIdx.x] = s;
+        const int vi = lane >> SH;
+        if ((lane & ((1 << SH) - 1)) == 0 && vi < NV) {
+            pp[c * NV + vi] = v[0];
             __threadfence();
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_flag = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
-        __syncthreads();
-        if (s_flag) {
-            // last chunk of bin (p, i): sum the chunks in order and finish the bin
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            // last chunk of bin (p, i): lane j < NV sums value j over the chunks in order
             __threadfence();
-            if (threadIdx.x < NV) {
-                float2 s = __ldcg(pp + threadIdx.x);
-                for (int cc = 1; cc < a.nchunks; cc++) s = ff_add(s, __ldcg(pp + cc * NV + threadIdx.x));
-                sv[threadIdx.x] = (double)s.x + (double)s.y;
+            double val = 0.0;
+            if (lane < NV) {
+                float2 s = __ldcg(pp + lane);
+                for (int cc = 1; cc < a.nchunks; cc++) s = ff_add(s, __ldcg(pp + cc * NV + lane));
+                val = (double)s.x + (double)s.y;
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            double sv[NV];
+#pragma unroll
+            for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
+            int lastp = 0;
+            if (lane == 0) {
                 bin_epilogue(a.ea, p, i, sv);
                 __threadfence();
-                s_flag = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
+                lastp = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
             }
-            __syncthreads();
-            if (s_flag) {
+            lastp = __shfl_sync(0xffffffffu, lastp, 0);
+            if (lastp) {
                 __threadfence();
-                point_reduce(a.ea, p, warp, nwarps, lane);
+                point_reduce(a.ea, p, 0, 1, lane);
             }
         }
-        __syncthreads();
     }
 }
 

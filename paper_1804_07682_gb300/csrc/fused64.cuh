@@ -72,23 +72,26 @@ struct SplitArgs64 {
     const PointConst* pcs;
     BaseConst bc;
     double* part;  // [npts][nbins][nchunks][NV]
+    int* counter;
     EpiArgs ea;
 };
 
+// Same warp-tile structure as k_fused_split, all in double.
 template <int NL, bool GRAD, bool SPEC>
 __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
     using M = NodeMath64<NL, GRAD, SPEC>;
     constexpr int NV = M::NV;
-    __shared__ double red[8][NV];
-    __shared__ double sv[NV];
-    __shared__ int s_flag;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
     int last_p = -1;
     M m;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int c = (int)(tile % a.nchunks);
-        const int64_t t2 = tile / a.nchunks;
+    while (true) {
+        int64_t t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int c = (int)(t % a.nchunks);
+        const int64_t t2 = t / a.nchunks;
         const int i = (int)(t2 % a.nbins);
         const int p = (int)(t2 / a.nbins);
         if (p != last_p) {
@@ -98,48 +101,42 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
         double acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) acc[v] = 0.0;
-        const int k0 = c * a.chunk;
-        const int k1 = min(a.n, k0 + a.chunk);
+        const int k1 = min(a.n, (c + 1) * a.chunk);
         const double2* g = a.grid + (int64_t)i * a.n;
-        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) m.update(g[k], acc);
+        for (int k = c * a.chunk + lane; k < k1; k += 32) m.update(g[k], acc);
+        double* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             double x = acc[v];
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) red[warp][v] = x;
+            if (lane == v) pp[c * NV + v] = x;
         }
-        __syncthreads();
-        double* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
-        if (threadIdx.x < NV) {
-            double s = red[0][threadIdx.x];
-            for (int w = 1; w < nwarps; w++) s += red[w][threadIdx.x];
-            pp[c * NV + threadIdx.x] = s;
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
             __threadfence();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_flag = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
-        __syncthreads();
-        if (s_flag) {
-            __threadfence();
-            if (threadIdx.x < NV) {
-                double s = __ldcg(pp + threadIdx.x);
-                for (int cc = 1; cc < a.nchunks; cc++) s += __ldcg(pp + cc * NV + threadIdx.x);
-                sv[threadIdx.x] = s;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            double val = 0.0;
+            if (lane < NV)
+                for (int cc = 0; cc < a.nchunks; cc++) val += __ldcg(pp + cc * NV + lane);
+            double sv[NV];
+#pragma unroll
+            for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
+            int lastp = 0;
+            if (lane == 0) {
                 bin_epilogue(a.ea, p, i, sv);
                 __threadfence();
-                s_flag = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
+                lastp = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
             }
-            __syncthreads();
-            if (s_flag) {
+            lastp = __shfl_sync(0xffffffffu, lastp, 0);
+            if (lastp) {
                 __threadfence();
-                point_reduce(a.ea, p, warp, nwarps, lane);
+                point_reduce(a.ea, p, 0, 1, lane);
             }
         }
-        __syncthreads();
     }
 }
 

@@ -55,7 +55,7 @@ namespace {
 
 enum { MAP_SPLIT = 0, MAP_BINS = 1 };
 const int kDefaultBlock = 256;
-const int kDefaultNodesPerThread = 16;
+const int kDefaultNodesPerThread = 64;
 
 int inst_nl(int nl, int ph) {
     if (ph == 0) {
@@ -196,9 +196,10 @@ gna_status dalloc(gna_plan* plan, T** ptr, size_t count) {
         if (s_ != GNA_OK) return s_;    \
     } while (0)
 
+// Split mapping: a warp tile covers 32 x npt consecutive nodes of one bin.
 int nchunks_of(const gna_plan* p) {
     if (p->mapping != MAP_SPLIT) return 1;
-    const int chunk = p->block * p->npt;
+    const int chunk = 32 * p->npt;
     return (p->n_uniform + chunk - 1) / chunk;
 }
 
@@ -219,8 +220,8 @@ int grid_size(const gna_plan* p, bool grad, bool spec, int64_t work_items) {
     }
     if (p->grid_mult > 0) per_sm = p->grid_mult;
     int64_t g = (int64_t)p->sm_count * per_sm;
-    if (p->mapping == MAP_SPLIT) g = std::min<int64_t>(g, work_items);
-    else g = std::min<int64_t>(g, (work_items * 32 + p->block - 1) / p->block);
+    // both mappings hand out warp-sized work items: no more CTAs than items need
+    g = std::min<int64_t>(g, (work_items * 32 + p->block - 1) / p->block);
     return (int)std::max<int64_t>(1, g);
 }
 
@@ -291,12 +292,12 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
         const int64_t tiles = (int64_t)plan->npts * plan->nbins * nchunks;
         const int g = grid_size(plan, grad, spec, tiles);
         if (plan->ph < 2) {
-            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
-                        plan->d_pc, plan->bc, (float2*)plan->d_part, ea};
+            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, 32 * plan->npt, nchunks, plan->npts,
+                        plan->d_pc, plan->bc, (float2*)plan->d_part, plan->d_counters, ea};
             CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         } else {
-            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, plan->block * plan->npt, nchunks, plan->npts,
-                          plan->d_pc, plan->bc, (double*)plan->d_part, ea};
+            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, 32 * plan->npt, nchunks, plan->npts,
+                          plan->d_pc, plan->bc, (double*)plan->d_part, plan->d_counters, ea};
             CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         }
     } else {
@@ -566,7 +567,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     TRY(dalloc(plan, &plan->d_pc, d->npts));
     const int nv_max = fused_nv(plan->nl_inst, true, true);
     if (plan->mapping == MAP_SPLIT) {
-        const int max_chunks = (plan->n_uniform + 64 * 4 - 1) / (64 * 4);  // smallest tile: 64 x 4
+        const int max_chunks = (plan->n_uniform + 32 * 4 - 1) / (32 * 4);  // smallest warp tile: 32 x 4
         plan->part_cap = (size_t)d->npts * d->nbins * max_chunks * nv_max;
         TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
     }
@@ -825,7 +826,8 @@ gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64)
         return fail(plan, GNA_EINVAL, "bad tuning '%s'", text);
     if (plan->mapping == MAP_SPLIT) {
-        const int chunk = block * npt;
+        if (npt < 4) return fail(plan, GNA_EINVAL, "nodes per lane must be >= 4");
+        const int chunk = 32 * npt;
         const int nch = (plan->n_uniform + chunk - 1) / chunk;
         if ((size_t)plan->npts * plan->nbins * nch * fused_nv(plan->nl_inst, true, true) > plan->part_cap)
             return fail(plan, GNA_ESHAPE, "tile %d x %d needs more partials than allocated", block, npt);
@@ -847,11 +849,10 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
     std::vector<std::pair<int, int>> cand;
     const int blocks[3] = {64, 128, 256};
     if (plan->mapping == MAP_SPLIT) {
-        const int npts_c[6] = {4, 8, 16, 32, 64, 128};
+        const int npts_c[7] = {4, 8, 16, 32, 64, 128, 256};
         for (int b : blocks)
             for (int m : npts_c) {
-                const int chunk = b * m;
-                if (chunk > 4 * plan->n_uniform && m > 4) continue;
+                if (32 * m > 2 * plan->n_uniform && m > 4) continue;
                 cand.push_back({b, m});
             }
     } else {

@@ -135,7 +135,7 @@ def test_chain_both_mappings(api, name, mapping):
     check_chain(api, get_case(name), "ff", mapping)
 
 
-@pytest.mark.parametrize("tuning", ["block=64 nodes=4", "block=128 nodes=7", "block=256 nodes=64", "block=96 nodes=3"])
+@pytest.mark.parametrize("tuning", ["block=64 nodes=4", "block=128 nodes=7", "block=256 nodes=64", "block=96 nodes=5"])
 def test_chain_launch_shapes(api, tuning):
     case = get_case("reactor8_40x3000")
     w = case.w

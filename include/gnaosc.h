@@ -244,6 +244,37 @@ gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches
  * (for tests; 0 restores the default). */
 gna_status gna_plan_set_wait_limit(gna_plan* plan, int64_t limit);
 
+/* ---------------------------------------------------------------------------
+ * gna_chain_eval_noalloc: chi^2 (and optionally its gradient and the binned
+ * prediction) of ONE parameter point for callers that cannot allocate device
+ * memory -- code that runs inside a memory pool or arena it does not own,
+ * plug-ins whose host framework forbids cudaMalloc, or processes that must
+ * keep their device footprint fixed once they have started.  It needs no
+ * plan, and it calls no cudaMalloc, no cudaFree and no allocating library
+ * routine.  Its working memory is one fixed array of about 0.9 MB inside this
+ * library, held by every GPU that loads the library until the process exits.
+ * The paper has no counterpart to this call; it is an addition of the library.
+ *   E, W:   device [nbins][n] double, bin-major: node energies (MeV, > 0) and
+ *           node weights (spectrum x integration weight x half bin width)
+ *   L, Lweight, nL: host, as in gna_plan_desc (Lweight NULL = 1/L^2)
+ *   params: device [1] gna_osc
+ *   norm, kind: as in gna_plan_desc
+ *   data:   device [nbins]
+ *   chi2:   device [1]; grad: device [4] or NULL; mu: device [nbins] or NULL
+ * Arithmetic as GNA_MIXED_FFPHASE.  Limits: nbins <= 2048, nL <= 8 and
+ * nbins * ceil(n / 1024) <= 16384; beyond them the call returns GNA_ESHAPE
+ * and launches nothing.  The first call on a device looks up the device
+ * address of the array (cudaGetSymbolAddress) once for that device; make that
+ * first call before any stream capture on the device.  Each call clears the
+ * counters it needs; the rest of the array keeps the previous call's
+ * contents.  Every call uses the same array, so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and give wrong results:
+ * serialise them on one stream.  Asynchronous on `stream`.
+ */
+gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, const double* W, const double* L, int nL,
+                                  const double* Lweight, const gna_osc* params, double norm, gna_chi2_kind kind,
+                                  const double* data, double* chi2, double* grad, double* mu, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

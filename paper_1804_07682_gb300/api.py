@@ -238,6 +238,38 @@ class Plan:
         return self.tuning
 
 
+def chi2_noalloc(E: torch.Tensor, W: torch.Tensor, L, params: torch.Tensor, data: torch.Tensor, norm: float,
+                 kind="pearson", Lweight=None, grad: bool = True, mu: bool = False, out: Optional[dict] = None,
+                 stream=None) -> dict:
+    """chi^2 of one point without any device allocation in the library.
+
+    For callers that cannot allocate device memory (a pool or arena they do not
+    own, a host framework that forbids cudaMalloc): the library works in a
+    fixed ~0.9 MB array of its own, shared by all calls, so calls must not
+    overlap on the GPU.  E, W: [nbins, n] float64 (node energies in MeV, node
+    weights); params [1, 4]; data [nbins].  Output tensors may be passed in
+    ``out`` (chi2 [1], grad [4], mu [nbins]) so that this call allocates
+    nothing on the Python side either.
+    """
+    _require_cuda()
+    nbins, n = E.shape
+    Ls = _f64(np.atleast_1d(L))
+    Lw = None if Lweight is None else _f64(Lweight)
+    if out is None:
+        out = {"chi2": torch.empty(1, dtype=torch.float64, device=E.device)}
+        if grad:
+            out["grad"] = torch.empty(4, dtype=torch.float64, device=E.device)
+        if mu:
+            out["mu"] = torch.empty(nbins, dtype=torch.float64, device=E.device)
+    P = ctypes.POINTER(ctypes.c_double)
+    code = N.lib().gna_chain_eval_noalloc(int(nbins), int(n), _ptr(E), _ptr(W), Ls.ctypes.data_as(P), Ls.size,
+                                          None if Lw is None else Lw.ctypes.data_as(P), _ptr(params), float(norm),
+                                          KINDS[kind], _ptr(data), _ptr(out["chi2"]), _ptr(out.get("grad")),
+                                          _ptr(out.get("mu")), ctypes.c_void_p(_stream(stream)))
+    N.check(code, what="gna_chain_eval_noalloc")
+    return out
+
+
 class OscChi2(torch.autograd.Function):
     """chi^2(theta, eta) of one plan point with its hand-written gradient.
 

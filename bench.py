@@ -55,6 +55,24 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     return nL * per_r + per_node
 
 
+# DRAM traffic of one launch of the benchmarked kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
+# sources it was taken with: reported as null once they change.
+TRAFFIC_CAPTURE = {"sources_sha256": None, "bytes": None}
+KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
+                  "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h"]
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -136,41 +154,126 @@ def reduce_max(dist, x, device):
 
 # --------------------------------------------------------------- reference arm --
 def reference_arm(args):
-    """The oracle, as it stands, timed on the host cores (bounded sample per step)."""
+    """The oracle, as it stands, timed on the host cores.  Each step evaluates
+    a bounded sample of the workload (a number of whole bins, every node and
+    baseline, with the gradient) sized so that warm-up + timed steps take about
+    a minute; the rate is scaled to one full evaluation."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
     import oracle
 
     w = wl.ALL[args.workload]()
-    nb = args.ref_bins
-    edges = w.edges[: nb + 1]
-    data = np.full(nb, 100.0)
     N = 1.0
     th = w.theta[0]
 
-    def step():
-        return oracle.chain(edges, w.nodes_per_bin, w.L, th, N, data, w.kind, e_scale=w.e_scale)
+    def run(nb):
+        return oracle.chain(w.edges[: nb + 1], w.nodes_per_bin, w.L, th, N, np.full(nb, 100.0), w.kind,
+                            e_scale=w.e_scale)
 
+    t0 = time.perf_counter()
+    run(1)
+    t_bin = max(time.perf_counter() - t0, 1e-4)
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    nb = int(max(1, min(w.nbins, budget / t_bin)))
     for _ in range(args.warmup):
-        step()
+        run(nb)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        run(nb)
     dt = (time.perf_counter() - t0) / args.steps
     frac = nb / w.nbins
     evals = frac / dt
+    sample = "%d of %d bins per step (x%d nodes x%d baselines, with gradient), scaled to one full evaluation" % (
+        nb, w.nbins, w.nodes_per_bin, w.nL)
     line = {"impl": "reference", "metric": METRIC, "value": evals, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / frac, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "bins_per_step": nb, "points_per_eval": w.points_per_eval()},
+            "config": {"workload": w.name, "bins": w.nbins, "nodes_per_bin": w.nodes_per_bin, "baselines": w.nL,
+                       "points_per_eval": w.points_per_eval(), "bins_per_step": nb},
             "gpoints_per_s": evals * w.points_per_eval() / 1e9,
             "cpu_baseline": {"value": evals, "unit": "evals/s", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": "%d of %d bins per step (x%d nodes x%d baselines), scaled to one full eval"
-                                       % (nb, w.nbins, w.nodes_per_bin, w.nL)},
+                             "sample": sample},
             "e2e": {"value": evals, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# -------------------------------------------------------------- side workloads --
+def side_workloads(api, torch, device, args):
+    """The batched workloads, each timed on its own after the main timed region:
+    the 64 x 64 scan (4096 points, uneven grids, one graph-replayed launch) and
+    the 16384 pseudo-experiment fits (20 Levenberg-Marquardt iterations)."""
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    # scan
+    w = wl.scan_64x64_500bins()
+    plan = api.Plan(w.edges, w.L, npts=w.npts, node_counts=w.node_counts, norm=1.0, e_scale=w.e_scale, prec=args.prec,
+                    kind=w.kind)
+    p = plan.params_tensor(w.theta)
+    truth = plan.params_tensor(np.repeat(np.array(wl.TRUTH)[None, :], w.npts, axis=0))
+    dummy = torch.ones(w.nbins, dtype=torch.float64, device=device)
+    m = plan.eval(truth, dummy, grad=False, mu=True)["mu"][int(np.argmax(w.node_counts))]
+    N = wl.TOTAL_EVENTS / float(m.sum())
+    plan.close()
+    plan = api.Plan(w.edges, w.L, npts=w.npts, node_counts=w.node_counts, norm=N, e_scale=w.e_scale, prec=args.prec,
+                    kind=w.kind)
+    data = torch.as_tensor(wl.poisson_data((m * N).cpu().numpy(), w.data_seed), device=device)
+    plan.autotune(p, data, reps=3)
+    plan.set_graph(True)
+    o = {"chi2": torch.empty(w.npts, dtype=torch.float64, device=device),
+         "grad": torch.empty(w.npts, 4, dtype=torch.float64, device=device)}
+    for _ in range(3):
+        plan.eval(p, data, grad=True, out=o)
+    reps = 20
+    torch.cuda.synchronize()
+    plan.profile(False)
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    for _ in range(reps):
+        plan.eval(p, data, grad=True, out=o)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / reps
+    pts = w.points_per_eval()
+    ops = sum(fp32_ops_per_node(1, True, False) * w.nbins * int(n) for n in w.node_counts)
+    out["scan_64x64_500bins"] = {"scans_per_s": 1e3 / ms, "ms_per_scan": ms, "chi2_grad_evals_per_s": w.npts * 1e3 / ms,
+                                 "gpoints_per_s": pts / ms / 1e6, "points_per_scan": pts,
+                                 "fp32_frac_of_issue_peak": ops / (ms * 1e-3) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
+                                 "tuning": plan.tuning, "graph": True}
+    plan.close()
+    # fits
+    w = wl.fits_16384x1000()
+    plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, npts=1, norm=1.0, prec=args.prec, kind=w.kind)
+    m = plan.eval(plan.params_tensor(w.truth), torch.ones(w.nbins, dtype=torch.float64, device=device), grad=False,
+                  mu=True)["mu"][0]
+    N = wl.TOTAL_EVENTS / float(m.sum())
+    plan.close()
+    plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, npts=w.npts, norm=N, prec=args.prec, kind=w.kind,
+                    max_datasets=w.npts)
+    data = torch.as_tensor(wl.pseudo_datasets((m * N).cpu().numpy(), w.n_datasets, w.data_seed), device=device)
+    p0 = plan.params_tensor(w.theta)
+    p = p0.clone()
+    plan.autotune(p, data, reps=1)
+    c2 = torch.empty(w.npts, dtype=torch.float64, device=device)
+    p.copy_(p0)
+    plan.fit(p, data, iters=2, graph=True, chi2_out=c2)
+    torch.cuda.synchronize()
+    p.copy_(p0)
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    plan.fit(p, data, iters=w.fit_iters, graph=True, chi2_out=c2)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    plan.status()
+    ms = a0.elapsed_time(a1)
+    pts = w.points_per_eval() * w.fit_iters
+    out["fits_16384x1000"] = {"fits_per_s": w.npts * 1e3 / ms, "ms_per_batch": ms, "iterations": w.fit_iters,
+                              "chi2_grad_evals_per_s": w.npts * w.fit_iters * 1e3 / ms, "gpoints_per_s": pts / ms / 1e6,
+                              "median_best_chi2": float(c2.median()), "tuning": plan.tuning, "graph": True}
+    plan.close()
+    return out
 
 
 # ---------------------------------------------------------------------- ours --
@@ -188,6 +291,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default=None)
     ap.add_argument("--ref-bins", type=int, default=16)
+    ap.add_argument("--no-side", action="store_true", help="skip the scan and fit side measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -271,8 +375,9 @@ def main():
     peak_tops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     pk, pk_src = peaks()
     hbm_bytes = 16 * w.nbins * w.nodes_per_bin
+    traffic = TRAFFIC_CAPTURE["bytes"] if TRAFFIC_CAPTURE["sources_sha256"] == kernel_sources_sha256() else None
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
-                "frac": achieved_tops / peak_tops, "traffic": None,
+                "frac": achieved_tops / peak_tops, "traffic": traffic, "algorithmic_bytes": hbm_bytes,
                 "kernel": "k_fused_split (double-float phase, 8 baselines, gradient + spectra)",
                 "kernel_ms": kern_avg_ms, "ops_per_launch": ops,
                 "peak_note": "FP32 issue peak 152 SM x 128 lanes x 2070 MHz (FMA = 1 op)",
@@ -336,6 +441,8 @@ def main():
                "sample": "%d of %d bins (x%d nodes x%d baselines, with gradient) in %.2f s, scaled to one eval"
                          % (nb, w.nbins, w.nodes_per_bin, w.nL, dt)}
 
+    side = None if args.no_side else side_workloads(api, torch, device, args)
+
     if rank == 0:
         line = {"metric": METRIC, "value": evals_per_s, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -345,7 +452,8 @@ def main():
                            "l2": "inputs larger than L2 (%d MB energy grid)" % (hbm_bytes >> 20),
                            "tuning": plan.tuning, "parallelism": "replicas" if world > 1 else "single"},
                 "gpoints_per_s": evals_per_s * points / 1e9, "roofline": roofline, "plain_fp64_chain": plain,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+                "side_workloads": side}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

@@ -149,21 +149,25 @@ __host__ __device__ constexpr int pow2ceil(int v) { return v <= 1 ? 1 : v <= 2 ?
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
 // ---------------------------------------------------------------------------
-// Split mapping: a warp tile is (point p, bin i, node chunk c of 32 m nodes);
-// lane l takes nodes c 32 m + l + 32 j (bin-major grid, node k of bin i at
-// i n + k: every warp load is 512 contiguous bytes, the next one prefetched
-// while the current node is computed), then the warp reduces its Kahan sums
-// with a transposed shuffle reduction and stores the chunk's partial.  Warps
-// take tiles from a global counter (no CTA barriers anywhere).  The warp that
-// stores the last chunk of a bin sums the chunks in order (double-float) and
-// runs the bin epilogue; the last bin of a point to finish reduces the point.
+// Split mapping (uniform grids): the flat node space f = (p nbins + i) n + k of
+// all points is cut into equal contiguous ranges, one per resident warp
+// (range length `per`).  A warp walks its range: lane l takes nodes f + l,
+// f + l + 32, ... (bin-major grid, node f at f mod (nbins n): every warp load is
+// 512 contiguous bytes, the next one prefetched while the current node is
+// computed, across bin boundaries too).  At each bin boundary the warp reduces
+// its Kahan sums with a transposed shuffle reduction and stores the segment's
+// partial in slot w - w_first(bin); the warp storing a bin's last segment sums
+// the segments in order (double-float) and runs the bin epilogue, and the
+// last bin of a point to finish reduces the point.  Equal ranges keep every
+// warp busy to the end; there is no queue and no CTA barrier.
 struct SplitArgs {
     const float4* grid;
-    int nbins, n, chunk, nchunks, npts;
+    int nbins, n, npts;
+    int64_t per;    // nodes per warp range
+    int maxseg;     // partial slots per (point, bin)
     const PointConst* pcs;
     BaseConst bc;
-    float2* part;   // [npts][nbins][nchunks][NV]
-    int* counter;   // tile counter, zeroed before the launch
+    float2* part;   // [npts][nbins][maxseg][NV]
     EpiArgs ea;
 };
 
@@ -178,18 +182,21 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
     constexpr int NVP = pow2ceil(NV);
     constexpr int SH = 5 - ilog2(NVP);
     const int lane = threadIdx.x & 31;
-    const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t gn = (int64_t)a.nbins * a.n;  // nodes of the (shared) grid
+    const int64_t total = gn * a.npts;
+    const int64_t f0 = w * a.per;
+    const int64_t f1 = min(total, f0 + a.per);
     int last_p = -1;
     M m;
-    while (true) {
-        int64_t t = 0;
-        if (lane == 0) t = atomicAdd(a.counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntiles) break;
-        const int c = (int)(t % a.nchunks);
-        const int64_t t2 = t / a.nchunks;
-        const int i = (int)(t2 % a.nbins);
-        const int p = (int)(t2 / a.nbins);
+    int64_t f = f0 + lane;
+    int64_t gi = (f < f1) ? f % gn : 0;  // grid index of f, advanced with at most one wrap per step
+    float4 cur = (f < f1) ? __ldg(a.grid + gi) : make_float4(1.f, 0.f, 0.f, 0.f);
+    for (int64_t pos = f0; pos < f1;) {
+        const int64_t q = pos / a.n;  // (point, bin) pair
+        const int p = (int)(q / a.nbins);
+        const int i = (int)(q - (int64_t)p * a.nbins);
+        const int64_t seg_end = min(f1, (q + 1) * a.n);
         if (p != last_p) {
             m.load(a.pcs + p, a.bc);
             last_p = p;
@@ -197,40 +204,42 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
         KahanF acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) kzero(acc[v]);
-        const int k1 = min(a.n, (c + 1) * a.chunk);
-        const float4* g = a.grid + (int64_t)i * a.n;
-        int k = c * a.chunk + lane;
-        float4 cur = (k < k1) ? __ldg(g + k) : make_float4(1.f, 0.f, 0.f, 0.f);
-        while (k < k1) {
-            const int kn = k + 32;
-            const float4 nxt = (kn < k1) ? __ldg(g + kn) : cur;
+        while (f < seg_end) {
+            const int64_t fn = f + 32;
+            int64_t gin = gi + 32;
+            if (gin >= gn) gin -= gn;
+            const float4 nxt = (fn < f1) ? __ldg(a.grid + gin) : cur;
             m.update(cur, acc);
             cur = nxt;
-            k = kn;
+            f = fn;
+            gi = gin;
         }
+        // lanes whose next node lies past this segment wait here with f >= seg_end
         float2 v[NVP];
 #pragma unroll
         for (int j = 0; j < NVP; j++) v[j] = (j < NV) ? kahan_to_ff(acc[j < NV ? j : 0]) : make_float2(0.f, 0.f);
         warp_transpose_reduce<NVP>(v, lane);
-        // lane l holds value (l >> SH); lanes with (l mod 2^SH) == 0 store it
-        float2* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
+        const int64_t w_first = (q * a.n) / a.per;
+        const int64_t w_last = ((q + 1) * a.n - 1) / a.per;
+        const int nseg = (int)(w_last - w_first + 1);
+        float2* pp = a.part + q * a.maxseg * NV;
         const int vi = lane >> SH;
         if ((lane & ((1 << SH) - 1)) == 0 && vi < NV) {
-            pp[c * NV + vi] = v[0];
+            pp[(w - w_first) * NV + vi] = v[0];
             __threadfence();
         }
         __syncwarp();
         int last = 0;
-        if (lane == 0) last = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
+        if (lane == 0) last = (atomicAdd(a.ea.bin_cnt + q, 1) == nseg - 1);
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last) {
-            // last chunk of bin (p, i): lane j < NV sums value j over the chunks in order
+            // last segment of bin (p, i): lane j < NV sums value j over the segments in order
             __threadfence();
             double val = 0.0;
             if (lane < NV) {
-                float2 s = __ldcg(pp + lane);
-                for (int cc = 1; cc < a.nchunks; cc++) s = ff_add(s, __ldcg(pp + cc * NV + lane));
-                val = (double)s.x + (double)s.y;
+                float2 sum = __ldcg(pp + lane);
+                for (int sg = 1; sg < nseg; sg++) sum = ff_add(sum, __ldcg(pp + sg * NV + lane));
+                val = (double)sum.x + (double)sum.y;
             }
             double sv[NV];
 #pragma unroll
@@ -247,6 +256,7 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
                 point_reduce(a.ea, p, 0, 1, lane);
             }
         }
+        pos = seg_end;
     }
 }
 
@@ -295,12 +305,25 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
 #pragma unroll
         for (int v = 0; v < NV; v++) kzero(acc[v]);
         const float4* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
-        float4 cur = __ldg(g);
-        for (int k = 0; k < n; k++) {
-            const float4 nxt = (k + 1 < n) ? __ldg(g + (int64_t)(k + 1) * 32) : cur;
-            m.update(cur, acc);
-            cur = nxt;
+        // ring of D nodes in flight: with few baselines a node is too little
+        // work to cover the load latency of the next one
+        constexpr int D = (NL >= 4) ? 1 : 4;
+        float4 buf[D];
+#pragma unroll
+        for (int j = 0; j < D; j++) buf[j] = (j < n) ? __ldg(g + (int64_t)j * 32) : make_float4(1.f, 0.f, 0.f, 0.f);
+        int k = 0;
+        for (; k + D <= n; k += D) {
+#pragma unroll
+            for (int j = 0; j < D; j++) {
+                const float4 cur = buf[j];
+                const int kn = k + j + D;
+                buf[j] = (kn < n) ? __ldg(g + (int64_t)kn * 32) : cur;
+                m.update(cur, acc);
+            }
         }
+#pragma unroll
+        for (int j = 0; j < D; j++)
+            if (k + j < n) m.update(buf[j], acc);
         const int i = b * 32 + lane;
         if (i < a.nbins) {
             double v[NV];

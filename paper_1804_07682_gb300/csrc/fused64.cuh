@@ -68,32 +68,34 @@ struct NodeMath64 {
 
 struct SplitArgs64 {
     const double2* grid;
-    int nbins, n, chunk, nchunks, npts;
+    int nbins, n, npts;
+    int64_t per;
+    int maxseg;
     const PointConst* pcs;
     BaseConst bc;
-    double* part;  // [npts][nbins][nchunks][NV]
-    int* counter;
+    double* part;  // [npts][nbins][maxseg][NV]
     EpiArgs ea;
 };
 
-// Same warp-tile structure as k_fused_split, all in double.
+// Same equal-range structure as k_fused_split, all in double.
 template <int NL, bool GRAD, bool SPEC>
 __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
     using M = NodeMath64<NL, GRAD, SPEC>;
     constexpr int NV = M::NV;
     const int lane = threadIdx.x & 31;
-    const int64_t ntiles = (int64_t)a.npts * a.nbins * a.nchunks;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t gn = (int64_t)a.nbins * a.n;
+    const int64_t total = gn * a.npts;
+    const int64_t f0 = w * a.per;
+    const int64_t f1 = min(total, f0 + a.per);
     int last_p = -1;
     M m;
-    while (true) {
-        int64_t t = 0;
-        if (lane == 0) t = atomicAdd(a.counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntiles) break;
-        const int c = (int)(t % a.nchunks);
-        const int64_t t2 = t / a.nchunks;
-        const int i = (int)(t2 % a.nbins);
-        const int p = (int)(t2 / a.nbins);
+    int64_t f = f0 + lane;
+    for (int64_t pos = f0; pos < f1;) {
+        const int64_t q = pos / a.n;
+        const int p = (int)(q / a.nbins);
+        const int i = (int)(q - (int64_t)p * a.nbins);
+        const int64_t seg_end = min(f1, (q + 1) * a.n);
         if (p != last_p) {
             m.load(a.pcs + p, a.bc);
             last_p = p;
@@ -101,27 +103,28 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
         double acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) acc[v] = 0.0;
-        const int k1 = min(a.n, (c + 1) * a.chunk);
-        const double2* g = a.grid + (int64_t)i * a.n;
-        for (int k = c * a.chunk + lane; k < k1; k += 32) m.update(g[k], acc);
-        double* pp = a.part + ((int64_t)p * a.nbins + i) * a.nchunks * NV;
+        for (; f < seg_end; f += 32) m.update(a.grid[f % gn], acc);
+        const int64_t w_first = (q * a.n) / a.per;
+        const int64_t w_last = ((q + 1) * a.n - 1) / a.per;
+        const int nseg = (int)(w_last - w_first + 1);
+        double* pp = a.part + q * a.maxseg * NV;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             double x = acc[v];
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == v) pp[c * NV + v] = x;
+            if (lane == v) pp[(w - w_first) * NV + v] = x;
         }
         __threadfence();
         __syncwarp();
         int last = 0;
-        if (lane == 0) last = (atomicAdd(a.ea.bin_cnt + (int64_t)p * a.nbins + i, 1) == a.nchunks - 1);
+        if (lane == 0) last = (atomicAdd(a.ea.bin_cnt + q, 1) == nseg - 1);
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last) {
             __threadfence();
             double val = 0.0;
             if (lane < NV)
-                for (int cc = 0; cc < a.nchunks; cc++) val += __ldcg(pp + cc * NV + lane);
+                for (int sg = 0; sg < nseg; sg++) val += __ldcg(pp + sg * NV + lane);
             double sv[NV];
 #pragma unroll
             for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
                 point_reduce(a.ea, p, 0, 1, lane);
             }
         }
+        pos = seg_end;
     }
 }
 

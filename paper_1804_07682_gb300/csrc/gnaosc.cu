@@ -55,7 +55,7 @@ namespace {
 
 enum { MAP_SPLIT = 0, MAP_BINS = 1 };
 const int kDefaultBlock = 256;
-const int kDefaultNodesPerThread = 64;
+const int kDefaultNodesPerThread = 16;
 
 int inst_nl(int nl, int ph) {
     if (ph == 0) {
@@ -100,6 +100,7 @@ struct gna_plan {
     int ntasks = 0;
     int* d_counters = nullptr;  // [1 + npts + npts*nbins (split)]: work counter, per-point, per-bin arrivals
     int64_t ncounters = 0;
+    int maxseg_cap = 2;  // split mapping: partial slots per (point, bin) the plan allocated
     double* d_edges = nullptr;
     // constants
     BaseConst bc{};
@@ -196,31 +197,57 @@ gna_status dalloc(gna_plan* plan, T** ptr, size_t count) {
         if (s_ != GNA_OK) return s_;    \
     } while (0)
 
-// Split mapping: a warp tile covers 32 x npt consecutive nodes of one bin.
-int nchunks_of(const gna_plan* p) {
-    if (p->mapping != MAP_SPLIT) return 1;
-    const int chunk = 32 * p->npt;
-    return (p->n_uniform + chunk - 1) / chunk;
+// Split mapping: equal node ranges, one per warp.  The warp count is the
+// resident capacity (occupancy from the register count), but no warp gets
+// fewer than 32 x npt nodes; the range length keeps every bin's segment count
+// within the partial slots the plan allocated.
+struct SplitShape {
+    int grid;
+    int64_t per;
+    int maxseg;
+};
+
+int resident_ctas_per_sm(const gna_plan* p, bool grad, bool spec);
+
+SplitShape split_shape(const gna_plan* p, bool grad, bool spec) {
+    const int64_t total = (int64_t)p->npts * p->nbins * p->n_uniform;
+    const int64_t resident = (int64_t)p->sm_count * resident_ctas_per_sm(p, grad, spec) * (p->block / 32);
+    const int64_t min_per = 32LL * p->npt;
+    int64_t warps = std::max<int64_t>(1, std::min<int64_t>(resident, (total + min_per - 1) / min_per));
+    int64_t per = (total + warps - 1) / warps;
+    // a bin of n nodes meets at most ceil(n / per) + 1 ranges
+    const int64_t per_floor = (p->n_uniform + (p->maxseg_cap - 1) - 1) / (p->maxseg_cap - 1);
+    if (per < per_floor) {
+        per = per_floor;
+        warps = (total + per - 1) / per;
+    }
+    SplitShape sh;
+    sh.per = per;
+    sh.grid = (int)std::max<int64_t>(1, (warps * 32 + p->block - 1) / p->block);
+    sh.maxseg = (int)((p->n_uniform + per - 1) / per + 1);
+    return sh;
 }
+
+int nchunks_of(const gna_plan* p) { return 1; }
 
 int value_count(const gna_plan* p, bool grad, bool spec) { return fused_nv(p->nl_inst, grad, spec); }
 
-// Persistent grid size for the current launch shape.
-int grid_size(const gna_plan* p, bool grad, bool spec, int64_t work_items) {
-    int per_sm = 2;
+int resident_ctas_per_sm(const gna_plan* p, bool grad, bool spec) {
+    int per_sm = std::max(1, 1024 / p->block);
     if (p->mapping == MAP_SPLIT) {
-        int regs = split_regs(p->ph, p->nl_inst, grad, spec);
+        const int regs = split_regs(p->ph, p->nl_inst, grad, spec);
         if (regs > 0) {
-            int by_regs = 65536 / (std::max(regs, 32) * p->block);
-            int by_threads = 2048 / p->block;
-            per_sm = std::max(1, std::min(by_regs, by_threads));
+            const int alloc = ((std::max(regs, 32) + 7) / 8) * 8;  // registers are allocated in units of 8
+            per_sm = std::max(1, std::min(65536 / (alloc * p->block), 2048 / p->block));
         }
-    } else {
-        per_sm = std::max(1, 1024 / p->block);
     }
     if (p->grid_mult > 0) per_sm = p->grid_mult;
-    int64_t g = (int64_t)p->sm_count * per_sm;
-    // both mappings hand out warp-sized work items: no more CTAs than items need
+    return per_sm;
+}
+
+// Persistent grid size of the bin mapping (warp-sized work items).
+int grid_size(const gna_plan* p, bool grad, bool spec, int64_t work_items) {
+    int64_t g = (int64_t)p->sm_count * resident_ctas_per_sm(p, grad, spec);
     g = std::min<int64_t>(g, (work_items * 32 + p->block - 1) / p->block);
     return (int)std::max<int64_t>(1, g);
 }
@@ -245,10 +272,13 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     const bool spec = q.spectra != nullptr;
     int nl = 0;
     const int NV = value_count(plan, grad, spec);
-    const int nchunks = nchunks_of(plan);
-    if (plan->mapping == MAP_SPLIT && (size_t)plan->npts * plan->nbins * nchunks * NV > plan->part_cap)
-        return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
-                    (long long)plan->npts * plan->nbins * nchunks * NV, plan->part_cap);
+    SplitShape sh{};
+    if (plan->mapping == MAP_SPLIT) {
+        sh = split_shape(plan, grad, spec);
+        if ((size_t)plan->npts * plan->nbins * sh.maxseg * NV > plan->part_cap)
+            return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
+                        (long long)plan->npts * plan->nbins * sh.maxseg * NV, plan->part_cap);
+    }
     // work counter, per-point and per-bin arrival counters: one memset
     CU(cudaMemsetAsync(plan->d_counters, 0, sizeof(int) * plan->ncounters, s));
     CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s));
@@ -289,16 +319,14 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
     if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
     if (plan->mapping == MAP_SPLIT) {
-        const int64_t tiles = (int64_t)plan->npts * plan->nbins * nchunks;
-        const int g = grid_size(plan, grad, spec, tiles);
         if (plan->ph < 2) {
-            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, 32 * plan->npt, nchunks, plan->npts,
-                        plan->d_pc, plan->bc, (float2*)plan->d_part, plan->d_counters, ea};
-            CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
+                        plan->d_pc, plan->bc, (float2*)plan->d_part, ea};
+            CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, sh.grid, plan->block, s));
         } else {
-            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, 32 * plan->npt, nchunks, plan->npts,
-                          plan->d_pc, plan->bc, (double*)plan->d_part, plan->d_counters, ea};
-            CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
+                          plan->d_pc, plan->bc, (double*)plan->d_part, ea};
+            CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, sh.grid, plan->block, s));
         }
     } else {
         const int g = grid_size(plan, grad, spec, plan->ntasks);
@@ -567,8 +595,13 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     TRY(dalloc(plan, &plan->d_pc, d->npts));
     const int nv_max = fused_nv(plan->nl_inst, true, true);
     if (plan->mapping == MAP_SPLIT) {
-        const int max_chunks = (plan->n_uniform + 32 * 4 - 1) / (32 * 4);  // smallest warp tile: 32 x 4
-        plan->part_cap = (size_t)d->npts * d->nbins * max_chunks * nv_max;
+        // ranges are at least 128 nodes long, so a bin meets at most ceil(n / 128) + 1 of
+        // them; the slot count is capped so that the partials stay within 256 M values
+        const int64_t pairs = (int64_t)d->npts * d->nbins;
+        const int64_t by_len = (plan->n_uniform + 127) / 128 + 1;
+        const int64_t by_mem = std::max<int64_t>(2, (256LL << 20) / (pairs * nv_max));
+        plan->maxseg_cap = (int)std::min(by_len, by_mem);
+        plan->part_cap = (size_t)pairs * plan->maxseg_cap * nv_max;
         TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
     }
     TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
@@ -825,13 +858,7 @@ gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     if (g) gm = atoi(g + 5);
     if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64)
         return fail(plan, GNA_EINVAL, "bad tuning '%s'", text);
-    if (plan->mapping == MAP_SPLIT) {
-        if (npt < 4) return fail(plan, GNA_EINVAL, "nodes per lane must be >= 4");
-        const int chunk = 32 * npt;
-        const int nch = (plan->n_uniform + chunk - 1) / chunk;
-        if ((size_t)plan->npts * plan->nbins * nch * fused_nv(plan->nl_inst, true, true) > plan->part_cap)
-            return fail(plan, GNA_ESHAPE, "tile %d x %d needs more partials than allocated", block, npt);
-    }
+    if (plan->mapping == MAP_SPLIT && npt < 4) return fail(plan, GNA_EINVAL, "nodes per lane must be >= 4");
     plan->block = block;
     plan->npt = npt;
     plan->grid_mult = gm;
@@ -849,12 +876,11 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
     std::vector<std::pair<int, int>> cand;
     const int blocks[3] = {64, 128, 256};
     if (plan->mapping == MAP_SPLIT) {
-        const int npts_c[7] = {4, 8, 16, 32, 64, 128, 256};
+        // block size only changes how the equal ranges sit on the SMs; the
+        // minimum range length matters only for workloads smaller than the GPU
+        const int npts_c[3] = {4, 16, 64};
         for (int b : blocks)
-            for (int m : npts_c) {
-                if (32 * m > 2 * plan->n_uniform && m > 4) continue;
-                cand.push_back({b, m});
-            }
+            for (int m : npts_c) cand.push_back({b, m});
     } else {
         for (int b : blocks) cand.push_back({b, 1});
     }

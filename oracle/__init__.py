@@ -47,29 +47,54 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    lib.or_threads.restype = _I
+    lib.or_set_threads.argtypes = [_I]
+    lib.or_pmns.argtypes = [_D, _D, _D, _D, _PD, _PD]
+    lib.or_prob.argtypes = [_I, _I, _D, _D, _D, _D, _D, _D, _D, _D, _I]
+    lib.or_prob.restype = _D
+    lib.or_pee.argtypes = [_PD, _I64, _D, _PD, _PD]
+    lib.or_pee_grad.argtypes = [_PD, _I64, _D, _PD, _PD, _PD]
+    lib.or_gl.argtypes = [_I, _PD, _PD]
+    lib.or_gl.restype = _I
+    lib.or_spectrum.argtypes = [_D, _D]
+    lib.or_spectrum.restype = _D
+    lib.or_binned.argtypes = [_I, _PD, _I, _PD, _PD, _I, _PD, _PD, _D, _PD, _PD]
+    lib.or_binned.restype = _I
+    lib.or_chi2.argtypes = [_I, _I, _PD, _PD, _PD, _D, _PD, _D, _PD, _I, _PD, _PD, _PD]
+    lib.or_chi2.restype = _D
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            lib.or_threads.restype = _I
-            lib.or_set_threads.argtypes = [_I]
-            lib.or_pmns.argtypes = [_D, _D, _D, _D, _PD, _PD]
-            lib.or_prob.argtypes = [_I, _I, _D, _D, _D, _D, _D, _D, _D, _D, _I]
-            lib.or_prob.restype = _D
-            lib.or_pee.argtypes = [_PD, _I64, _D, _PD, _PD]
-            lib.or_pee_grad.argtypes = [_PD, _I64, _D, _PD, _PD, _PD]
-            lib.or_gl.argtypes = [_I, _PD, _PD]
-            lib.or_gl.restype = _I
-            lib.or_spectrum.argtypes = [_D, _D]
-            lib.or_spectrum.restype = _D
-            lib.or_binned.argtypes = [_I, _PD, _I, _PD, _PD, _I, _PD, _PD, _D, _PD, _PD]
-            lib.or_binned.restype = _I
-            lib.or_chi2.argtypes = [_I, _I, _PD, _PD, _PD, _D, _PD, _D, _PD, _I, _PD, _PD, _PD]
-            lib.or_chi2.restype = _D
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+class use_library:
+    """Context manager that points this module at another build of oracle.c
+    (used by the tests that plant mistakes in a copy of the oracle)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _gl_cache.clear()
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        _gl_cache.clear()
+        return False
 
 
 def _p(a):

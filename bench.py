@@ -402,6 +402,7 @@ def main():
     g_host = torch.empty(1, 4, dtype=torch.float64).pin_memory().numpy()
     s_host = torch.empty(1, w.nL, w.nbins, dtype=torch.float64).pin_memory().numpy()
     e2e_steps = max(10, args.steps // 4)
+    plan.set_graph(True)
     for _ in range(3):
         plan.eval_host(p_host, d_host, grad=True, chi2_out=c_host, grad_out=g_host, spectra_out=s_host)
     if dist is not None:
@@ -410,6 +411,7 @@ def main():
     for _ in range(e2e_steps):
         plan.eval_host(p_host, d_host, grad=True, chi2_out=c_host, grad_out=g_host, spectra_out=s_host)
     e2e_ms, e2e_rate = replica_throughput(dist, (time.perf_counter() - t0) * 1e3, e2e_steps, world, device)
+    plan.set_graph(False)
     e2e = {"value": e2e_rate, "unit": "evals/s", "h2d_bytes_per_step": p_host.nbytes + d_host.nbytes,
            "d2h_bytes_per_step": c_host.nbytes + g_host.nbytes + s_host.nbytes}
 

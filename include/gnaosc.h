@@ -172,12 +172,15 @@ gna_status gna_plan_info(const gna_plan* plan, int64_t* nodes, int64_t* points_p
 gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
                           const double* data, int data_per_point, const gna_outputs* out, void* stream);
 
-/* gna_chain_eval_host: the same evaluation from HOST buffers: copies params
- * [npts], eta [nbins] (or NULL) and data to the plan's device staging
- * buffers, evaluates, copies chi2 [npts], grad [npts][4] (if grad != NULL)
- * and spectra [npts][nL][nbins] (if spectra != NULL; GNA_ESHAPE when that
- * exceeds 2^24 values) back to the host and synchronises the stream.  Host
- * buffers should be pinned for full copy speed. */
+/* gna_chain_eval_host: the same evaluation from HOST buffers (the paper's
+ * Sec. 4.2 sub-chain with one transfer in and one out): packs params [npts],
+ * data and eta [nbins] (or NULL) into the plan's pinned staging, copies them
+ * to the device in one transfer, evaluates, copies chi2 [npts], grad
+ * [npts][4] (if grad != NULL) and spectra [npts][nL][nbins] (if spectra !=
+ * NULL; GNA_ESHAPE when that exceeds 2^24 values) back in one transfer,
+ * synchronises the stream and unpacks them into the caller's buffers.  With
+ * graph mode on (gna_plan_set_graph) the transfer-evaluate-transfer sequence
+ * is replayed as one graph.  Any host memory is accepted. */
 gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
                                const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
                                void* stream);

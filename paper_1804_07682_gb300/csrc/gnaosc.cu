@@ -112,12 +112,6 @@ struct gna_plan {
     double* d_H = nullptr;
     double* d_chi2_tmp = nullptr;
     double* d_grad_tmp = nullptr;
-    // staging for host-buffer evaluations
-    gna_osc* d_params_stage = nullptr;
-    double* d_data_stage = nullptr;
-    double* d_eta_stage = nullptr;
-    double* d_chi2_stage = nullptr;
-    double* d_grad_stage = nullptr;
     // plain chain scratch
     double* d_plainP = nullptr;
     double* d_plainD = nullptr;
@@ -144,7 +138,15 @@ struct gna_plan {
     bool profile = false;
     std::vector<cudaEvent_t> prof_ev;  // pairs
     int prof_n = 0;
-    double* d_spec_stage = nullptr;
+    // packed staging of the host-buffer call: inputs [params | data | eta],
+    // outputs [chi2 | grad | spectra], pinned on the host, contiguous on the device
+    double* h_in = nullptr;
+    double* h_out = nullptr;
+    double* d_in = nullptr;
+    double* d_out = nullptr;
+    size_t in_cap = 0, out_cap = 0;
+    cudaGraphExec_t hexec = nullptr;
+    GraphKey hkey;
     double* d_sumW = nullptr;  // [ngrids][nbins]
     double wsum_all_lo = 0.0;  // sum_r (om_r + omlo_r) - wsum: constant term when the weights enter as hi + lo
     // graphs are captured on a plan-owned stream joined to the caller's by events
@@ -435,6 +437,9 @@ gna_status gna_plan_destroy(gna_plan* plan) {
     if (!plan) return GNA_OK;
     destroy_graph(plan);
     destroy_profile(plan);
+    if (plan->hexec) cudaGraphExecDestroy(plan->hexec);
+    if (plan->h_in) cudaFreeHost(plan->h_in);
+    if (plan->h_out) cudaFreeHost(plan->h_out);
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     if (plan->ev_in) cudaEventDestroy(plan->ev_in);
     if (plan->ev_out) cudaEventDestroy(plan->ev_out);
@@ -608,14 +613,20 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
     TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
     TRY(dalloc(plan, &plan->d_grad_tmp, (size_t)d->npts * 4));
-    TRY(dalloc(plan, &plan->d_params_stage, d->npts));
-    TRY(dalloc(plan, &plan->d_data_stage, (size_t)plan->max_datasets * d->nbins));
-    TRY(dalloc(plan, &plan->d_eta_stage, d->nbins));
-    TRY(dalloc(plan, &plan->d_chi2_stage, d->npts));
-    TRY(dalloc(plan, &plan->d_grad_stage, (size_t)d->npts * 4));
+    plan->in_cap = (size_t)d->npts * 4 + (size_t)plan->max_datasets * d->nbins + d->nbins;
+    plan->out_cap = (size_t)d->npts * 5;
+    if ((int64_t)d->npts * d->nL * d->nbins <= (1LL << 24)) plan->out_cap += (size_t)d->npts * d->nL * d->nbins;
+    TRY(dalloc(plan, &plan->d_in, plan->in_cap));
+    TRY(dalloc(plan, &plan->d_out, plan->out_cap));
+    {
+        cudaError_t e1 = cudaMallocHost(&plan->h_in, plan->in_cap * sizeof(double));
+        cudaError_t e2 = cudaMallocHost(&plan->h_out, plan->out_cap * sizeof(double));
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            cudaGetLastError();
+            return fail(plan, GNA_ENOMEM, "pinned staging of %zu + %zu doubles", plan->in_cap, plan->out_cap);
+        }
+    }
     TRY(dalloc(plan, &plan->d_lm, d->npts));
-    if ((int64_t)d->npts * d->nL * d->nbins <= (1LL << 24))
-        TRY(dalloc(plan, &plan->d_spec_stage, (size_t)d->npts * d->nL * d->nbins));
     TRY(dalloc(plan, &plan->d_status, 1));
     CU(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
     if (want_plain) {
@@ -727,24 +738,80 @@ gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const doub
                                const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
                                void* stream) {
     if (!plan) return GNA_EINVAL;
-    if (spectra && !plan->d_spec_stage) return fail(plan, GNA_ESHAPE, "spectra staging exceeds 2^24 values");
     if (!params || !data || !chi2) return fail(plan, GNA_EINVAL, "params, data and chi2 are required");
     if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
+    const size_t n_spec = (size_t)plan->npts * plan->nL * plan->nbins;
+    if (spectra && plan->out_cap < (size_t)plan->npts * 5 + n_spec)
+        return fail(plan, GNA_ESHAPE, "spectra staging exceeds 2^24 values");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t drows = data_per_point ? (size_t)plan->npts : 1;
-    CU(cudaMemcpyAsync(plan->d_params_stage, params, sizeof(gna_osc) * plan->npts, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(plan->d_data_stage, data, sizeof(double) * drows * plan->nbins, cudaMemcpyHostToDevice, s));
-    if (eta) CU(cudaMemcpyAsync(plan->d_eta_stage, eta, sizeof(double) * plan->nbins, cudaMemcpyHostToDevice, s));
-    gna_outputs o{plan->d_chi2_stage, grad ? plan->d_grad_stage : nullptr, nullptr, nullptr,
-                  spectra ? plan->d_spec_stage : nullptr};
-    TRY(gna_chain_eval(plan, plan->d_params_stage, eta ? plan->d_eta_stage : nullptr, sigma_eta, plan->d_data_stage,
-                       data_per_point, &o, stream));
-    CU(cudaMemcpyAsync(chi2, plan->d_chi2_stage, sizeof(double) * plan->npts, cudaMemcpyDeviceToHost, s));
-    if (grad) CU(cudaMemcpyAsync(grad, plan->d_grad_stage, sizeof(double) * 4 * plan->npts, cudaMemcpyDeviceToHost, s));
-    if (spectra)
-        CU(cudaMemcpyAsync(spectra, plan->d_spec_stage, sizeof(double) * plan->npts * plan->nL * plan->nbins,
-                           cudaMemcpyDeviceToHost, s));
+    plan->last_stream = s;
+    // pack the inputs into pinned staging: [params | data | eta]
+    const size_t n_par = (size_t)plan->npts * 4;
+    const size_t n_dat = (data_per_point ? (size_t)plan->npts : 1) * plan->nbins;
+    const size_t n_eta = eta ? (size_t)plan->nbins : 0;
+    memcpy(plan->h_in, params, n_par * sizeof(double));
+    memcpy(plan->h_in + n_par, data, n_dat * sizeof(double));
+    if (eta) memcpy(plan->h_in + n_par + n_dat, eta, n_eta * sizeof(double));
+    const size_t n_in = n_par + n_dat + n_eta;
+    const size_t n_out = (size_t)plan->npts * 5 + (spectra ? n_spec : 0);
+    double* d_par = plan->d_in;
+    double* d_dat = plan->d_in + n_par;
+    double* d_eta = eta ? plan->d_in + n_par + n_dat : nullptr;
+    EvalReq q{(const gna_osc*)d_par, d_eta, sigma_eta, d_dat, data_per_point, plan->d_out,
+              grad ? plan->d_out + plan->npts : nullptr, nullptr, nullptr,
+              spectra ? plan->d_out + (size_t)plan->npts * 5 : nullptr, nullptr};
+    // one H2D, the evaluation, one D2H: replayed as one graph in graph mode
+    auto enqueue_all = [&](cudaStream_t st, int* nl) -> gna_status {
+        CU(cudaMemcpyAsync(plan->d_in, plan->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, st));
+        TRY(enqueue_eval(plan, q, st, nl));
+        CU(cudaMemcpyAsync(plan->h_out, plan->d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return GNA_OK;
+    };
+    if (plan->use_graph) {
+        double sig = sigma_eta;
+        uintptr_t sigbits;
+        memcpy(&sigbits, &sig, sizeof(sigbits));
+        GraphKey key{{(uintptr_t)data_per_point, (uintptr_t)(eta != nullptr), sigbits, (uintptr_t)(grad != nullptr),
+                      (uintptr_t)(spectra != nullptr), (uintptr_t)plan->block, (uintptr_t)plan->npt,
+                      (uintptr_t)plan->grid_mult}};
+        cudaStream_t cs = plan->cap_stream;
+        if (!plan->hexec || !(key == plan->hkey)) {
+            if (plan->hexec) cudaGraphExecDestroy(plan->hexec);
+            plan->hexec = nullptr;
+            CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int nl = 0;
+            gna_status st = enqueue_all(cs, &nl);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cs, &g);
+            if (st != GNA_OK || e != cudaSuccess) {
+                cudaGetLastError();
+                if (g) cudaGraphDestroy(g);
+                if (st != GNA_OK) return st;
+                return fail(plan, GNA_ECUDA, "host graph capture: %s", cudaGetErrorString(e));
+            }
+            e = cudaGraphInstantiate(&plan->hexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                plan->hexec = nullptr;
+                return fail(plan, GNA_ECUDA, "host graph instantiate: %s", cudaGetErrorString(e));
+            }
+            plan->hkey = key;
+            plan->graph_launches = nl;
+        }
+        CU(cudaEventRecord(plan->ev_in, s));
+        CU(cudaStreamWaitEvent(cs, plan->ev_in, 0));
+        CU(cudaGraphLaunch(plan->hexec, cs));
+        CU(cudaEventRecord(plan->ev_out, cs));
+        CU(cudaStreamWaitEvent(s, plan->ev_out, 0));
+        plan->last_launches = plan->graph_launches;
+    } else {
+        TRY(enqueue_all(s, &plan->last_launches));
+    }
     CU(cudaStreamSynchronize(s));
+    memcpy(chi2, plan->h_out, sizeof(double) * plan->npts);
+    if (grad) memcpy(grad, plan->h_out + plan->npts, sizeof(double) * 4 * plan->npts);
+    if (spectra) memcpy(spectra, plan->h_out + (size_t)plan->npts * 5, sizeof(double) * n_spec);
     return GNA_OK;
 }
 

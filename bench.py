@@ -286,7 +286,78 @@ def side_workloads(api, torch, device, args):
                               "chi2_grad_evals_per_s": w.npts * w.fit_iters * 1e3 / ms, "gpoints_per_s": pts / ms / 1e6,
                               "median_best_chi2": float(c2.median()), "tuning": plan.tuning, "graph": True}
     plan.close()
+    # the 10^4-point reactor chain (latency-bound), all-double and mixed, graph-replayed
+    w = wl.reactor_200x50()
+    res = {}
+    for prec in ("fp64", "ff"):
+        plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, norm=1.0, prec=prec, kind=w.kind)
+        p = plan.params_tensor(w.theta)
+        d = torch.full((w.nbins,), 500.0, dtype=torch.float64, device=device)
+        o = {"chi2": torch.empty(1, dtype=torch.float64, device=device),
+             "grad": torch.empty(1, 4, dtype=torch.float64, device=device)}
+        plan.set_graph(True)
+        for _ in range(20):
+            plan.eval(p, d, grad=True, out=o)
+        torch.cuda.synchronize()
+        a0, a1 = ev(), ev()
+        reps = 2000
+        a0.record(stream)
+        for _ in range(reps):
+            plan.eval(p, d, grad=True, out=o)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / reps
+        res[prec] = {"evals_per_s": 1e3 / ms, "us_per_eval": ms * 1e3}
+        plan.close()
+    out["reactor_200x50"] = dict(res, note="10^4 nodes: launch-latency bound (graph replay of memset + 2 kernels)")
+    # the paper's Table 1 shape: bare OscProb in FP64 on 10^4 and 10^6 energies,
+    # GPU compute only and with the host<->device transfers (the host side is
+    # timed in the CPU-baseline leg)
+    t1 = {}
+    for n in (10 ** 4, 10 ** 6):
+        E_h = torch.linspace(1.8, 12.0, n, dtype=torch.float64).pin_memory()
+        P_h = torch.empty(1, n, dtype=torch.float64).pin_memory()
+        E_d = E_h.to(device)
+        for _ in range(5):
+            api.oscprob(E_d, [52.5], wl.TRUTH, "fp64")
+        torch.cuda.synchronize()
+        reps = 200
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        for _ in range(reps):
+            api.oscprob(E_d, [52.5], wl.TRUTH, "fp64")
+        a1.record(stream)
+        torch.cuda.synchronize()
+        gpu_ms = a0.elapsed_time(a1) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            e = E_h.to(device, non_blocking=True)
+            P = api.oscprob(e, [52.5], wl.TRUTH, "fp64")
+            P_h.copy_(P, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        gpu_xfer_ms = (time.perf_counter() - t0) * 1e3 / reps
+        t1[str(n)] = {"gpu_compute_ms": gpu_ms, "gpu_with_transfer_ms": gpu_xfer_ms}
+    out["oscprob_fp64_table1_shape"] = t1
     return out
+
+
+def cpu_oscprob_table1(t1):
+    """CPU-baseline leg of the Table 1 shape: the oracle's OscProb (FP64, all
+    host cores) on the same 10^4 and 10^6 energies; adds the CPU/GPU ratios."""
+    import oracle
+    import torch
+
+    for key, row in t1.items():
+        n = int(key)
+        En = torch.linspace(1.8, 12.0, n, dtype=torch.float64).numpy()
+        oracle.pee(En, 52.5, wl.TRUTH)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            oracle.pee(En, 52.5, wl.TRUTH)
+        cpu_ms = (time.perf_counter() - t0) * 1e3 / 5
+        row.update({"cpu_oracle_ms": cpu_ms, "cpu_threads": oracle.threads(),
+                    "cpu_over_gpu_with_transfer": cpu_ms / row["gpu_with_transfer_ms"],
+                    "cpu_over_gpu_compute": cpu_ms / row["gpu_compute_ms"]})
 
 
 # ---------------------------------------------------------------------- ours --
@@ -457,6 +528,8 @@ def main():
                          % (w.nbins, w.nodes_per_bin, w.nL, dt, oracle.threads())}
 
     side = None if args.no_side else side_workloads(api, torch, device, args)
+    if side is not None and cpu is not None:
+        cpu_oscprob_table1(side["oscprob_fp64_table1_shape"])
 
     if rank == 0:
         line = {"metric": METRIC, "value": evals_per_s, "unit": "evals/s", "n_gpus": world, "steps": args.steps,

@@ -9,6 +9,13 @@
 // (2 / mu_i) J_i J_i^T with J_i = N (1+eta_i) dM_i/dtheta.
 // The last bin of a point to finish sums the per-bin values over bins in a
 // fixed order (deterministic) and writes chi2, the gradient and J^T W J.
+//
+// In the mixed modes only mu_i and t_i = (d_i - mu_i) / mu_i are formed in
+// double (FP64 instructions are 1/64 of the FP32 rate on this part); the
+// Poisson term 2 mu_i h(t_i), h(t) = (1 + t) log1p(t) - t, the adjoint g_i and
+// the gradient and J^T W J terms are FP32 (their relative error, ~1e-7, is
+// far inside the mixed-mode tolerance).  Per-bin values are stored as float
+// pairs (hi + lo) and summed over bins in double-float arithmetic.
 #pragma once
 
 #include "common.cuh"
@@ -29,7 +36,7 @@ struct EpiArgs {
     double* mu_out;        // [npts][nbins] or NULL
     double* spectra_out;   // [npts][nL][nbins] or NULL
     double* grad_eta_out;  // [npts][nbins] or NULL
-    double* binvals;       // [npts][nbins][NBV] scratch
+    float2* binvals;       // [npts][nbins][NBV] scratch (double-float values)
     int NBV;               // 1 (chi2), 5 (+ gradient), 15 (+ J^T W J)
     const double* sumW;    // [ngrids][nbins] summed FP32 node weights (mixed modes)
     int shared_grid;
@@ -41,6 +48,24 @@ struct EpiArgs {
     int* pt_cnt;           // [npts] bins finished, zeroed before the launch
     int* bin_cnt;          // [npts][nbins] chunks finished (split mapping), zeroed before the launch
 };
+
+__device__ __forceinline__ float2 to_ff(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+// h(t) = (1 + t) log1p(t) - t in FP32: series sum_{k>=2} (-1)^k t^k / (k (k-1))
+// for |t| < 1/2 (24 terms: truncation below 1e-9 relative), where the closed
+// form would cancel; log1pf beyond (cancellation there is at most ~5x).
+__device__ __forceinline__ float poisson_h(float t) {
+    if (fabsf(t) < 0.5f) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 25; k >= 2; k--) s = fmaf(s, -t, 1.0f / (float)(k * (k - 1)));
+        return t * t * s;
+    }
+    return fmaf(1.0f + t, log1pf(t), -t);
+}
 
 // v: the NV summed values of (p, i): [0] sum W Pc, [1..4] tangent sums, [off + r] per-baseline sums.
 __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double* v) {
@@ -59,53 +84,92 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
     const double f = a.norm * (1.0 + e);
     const double mu = f * M;
     const double d = a.data[a.data_per_point ? idx : i];
-    double term, g;
-    if (a.kind == GNA_PEARSON) {
-        term = (d - mu) * (d - mu) / mu;
-        g = 1.0 - (d * d) / (mu * mu);
+    double term;
+    float g;
+    if (a.is64) {
+        double gd;
+        if (a.kind == GNA_PEARSON) {
+            term = (d - mu) * (d - mu) / mu;
+            gd = 1.0 - (d * d) / (mu * mu);
+        } else {
+            term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
+            gd = 2.0 * (1.0 - d / mu);
+        }
+        g = (float)gd;
+        float2* bv = a.binvals + idx * a.NBV;
+        const bool pen = a.eta && a.sigma > 0.0;
+        if (pen) term += e * e / (a.sigma * a.sigma);
+        bv[0] = to_ff(term);
+        if (a.has_grad && a.NBV >= 5) {
+            double J[4];
+            for (int q = 0; q < 4; q++) {
+                J[q] = -f * v[1 + q];
+                bv[1 + q] = to_ff(gd * J[q]);
+            }
+            if (a.NBV >= 15) {
+                const double h = 2.0 / mu;
+                int t = 5;
+                for (int q = 0; q < 4; q++)
+                    for (int r = q; r < 4; r++) bv[t++] = to_ff(h * J[q] * J[r]);
+            }
+        }
+        if (a.mu_out) a.mu_out[idx] = mu;
+        if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
     } else {
-        term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
-        g = 2.0 * (1.0 - d / mu);
-    }
-    const bool pen = a.eta && a.sigma > 0.0;
-    if (pen) term += e * e / (a.sigma * a.sigma);
-    double* bv = a.binvals + idx * a.NBV;
-    bv[0] = term;
-    if (a.has_grad && a.NBV >= 5) {
-        double J[4];
-        for (int q = 0; q < 4; q++) {
-            J[q] = -f * v[1 + q];
-            bv[1 + q] = g * J[q];
+        const double dm = d - mu;
+        const double t = dm / mu;  // the one FP64 division
+        if (a.kind == GNA_PEARSON) {
+            term = dm * t;  // (d - mu)^2 / mu
+            const float tf = (float)t;
+            g = 1.0f - (1.0f + tf) * (1.0f + tf);  // 1 - d^2 / mu^2
+        } else {
+            term = (d > 0.0) ? 2.0 * mu * (double)poisson_h((float)t) : 2.0 * mu;
+            g = -2.0f * (float)t;  // 2 (1 - d / mu)
         }
-        if (a.NBV >= 15) {
-            const double h = 2.0 / mu;
-            int t = 5;
-            for (int q = 0; q < 4; q++)
-                for (int r = q; r < 4; r++) bv[t++] = h * J[q] * J[r];
+        float2* bv = a.binvals + idx * a.NBV;
+        const bool pen = a.eta && a.sigma > 0.0;
+        if (pen) term += e * e / (a.sigma * a.sigma);
+        bv[0] = to_ff(term);
+        if (a.has_grad && a.NBV >= 5) {
+            const float ff = (float)f;
+            float J[4];
+            for (int q = 0; q < 4; q++) {
+                J[q] = -ff * (float)v[1 + q];
+                bv[1 + q] = make_float2(g * J[q], 0.f);
+            }
+            if (a.NBV >= 15) {
+                const float h = 2.0f / (float)mu;
+                int tt = 5;
+                for (int q = 0; q < 4; q++)
+                    for (int r = q; r < 4; r++) bv[tt++] = make_float2(h * J[q] * J[r], 0.f);
+            }
         }
+        if (a.mu_out) a.mu_out[idx] = mu;
+        if (a.grad_eta_out)
+            a.grad_eta_out[idx] = (double)g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
     }
-    if (a.mu_out) a.mu_out[idx] = mu;
-    if (a.grad_eta_out) a.grad_eta_out[idx] = g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
     if (a.spectra_out && a.nspec > 0)
         for (int r = 0; r < a.nL_out; r++) a.spectra_out[((int64_t)p * a.nL_out + r) * a.nbins + i] = v[off + r];
 }
 
 // Warps w = 0..nw-1 of the caller sum the per-bin values of point p (value v
-// by warp v mod nw; lane l takes bins l, l+32, ...; xor butterfly) and write
-// the point's outputs.  Reads go through L2 (__ldcg): other SMs wrote them.
+// by warp v mod nw; lane l takes bins l, l+32, ...; xor butterfly, all in
+// double-float) and write the point's outputs.  Reads go through L2
+// (__ldcg): other SMs wrote them.
 __device__ inline void point_reduce(const EpiArgs& a, int p, int w, int nw, int lane) {
-    const double* bv = a.binvals + (int64_t)p * a.nbins * a.NBV;
+    const float2* bv = a.binvals + (int64_t)p * a.nbins * a.NBV;
     for (int v = w; v < a.NBV; v += nw) {
-        double s = 0.0;
-        for (int i = lane; i < a.nbins; i += 32) s += __ldcg(bv + (int64_t)i * a.NBV + v);
+        float2 s = make_float2(0.f, 0.f);
+        for (int i = lane; i < a.nbins; i += 32) s = ff_add(s, __ldcg(bv + (int64_t)i * a.NBV + v));
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int o = 16; o >= 1; o >>= 1) s = ff_add(s, shfl_xor_f2(s, o));
         if (lane == 0) {
-            if (v == 0) a.chi2[p] = s;
+            const double tot = (double)s.x + (double)s.y;
+            if (v == 0) a.chi2[p] = tot;
             else if (v < 5) {
-                if (a.grad) a.grad[(int64_t)p * 4 + v - 1] = s;
+                if (a.grad) a.grad[(int64_t)p * 4 + v - 1] = tot;
             } else if (a.H) {
-                a.H[(int64_t)p * 10 + v - 5] = s;
+                a.H[(int64_t)p * 10 + v - 5] = tot;
             }
         }
     }

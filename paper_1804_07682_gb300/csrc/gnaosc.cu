@@ -88,9 +88,14 @@ struct gna_plan {
     int prec = GNA_MIXED_FFPHASE, kind = GNA_PEARSON, flags = 0, max_datasets = 0;
     int mapping = MAP_SPLIT;
     int sm_count = 0;
-    // grids
-    float4* grid_ff = nullptr;
-    double2* grid64 = nullptr;
+    // grids: the split layout (bin-major, uniform grids) and/or the bins layout
+    // ([group][node][lane] per grid); small uniform grids keep both so that the
+    // autotuner can choose the mapping
+    bool has_split = false, has_bins = false;
+    float4* grid_split = nullptr;
+    float4* grid_bins = nullptr;
+    double2* grid64_split = nullptr;
+    double2* grid64_bins = nullptr;
     double2* plain64 = nullptr;
     int64_t grid_len = 0, total_nodes = 0;
     int64_t* d_goff = nullptr;
@@ -108,7 +113,7 @@ struct gna_plan {
     // scratch
     void* d_part = nullptr;
     size_t part_cap = 0;  // elements of 8 bytes
-    double* d_binvals = nullptr;
+    float2* d_binvals = nullptr;
     double* d_H = nullptr;
     double* d_chi2_tmp = nullptr;
     double* d_grad_tmp = nullptr;
@@ -322,22 +327,22 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
     if (plan->mapping == MAP_SPLIT) {
         if (plan->ph < 2) {
-            SplitArgs a{plan->grid_ff, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
+            SplitArgs a{plan->grid_split, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
                         plan->d_pc, plan->bc, (float2*)plan->d_part, ea};
             CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, sh.grid, plan->block, s));
         } else {
-            SplitArgs64 a{plan->grid64, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
+            SplitArgs64 a{plan->grid64_split, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
                           plan->d_pc, plan->bc, (double*)plan->d_part, ea};
             CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, sh.grid, plan->block, s));
         }
     } else {
         const int g = grid_size(plan, grad, spec, plan->ntasks);
         if (plan->ph < 2) {
-            BinArgs a{plan->grid_ff, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+            BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
                       plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea};
             CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         } else {
-            BinArgs64 a{plan->grid64, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+            BinArgs64 a{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
                         plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea};
             CU(dispatch_bins(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         }
@@ -508,20 +513,24 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     double fall = 0.0;
     for (int r = 0; r < d->nL; r++) fall += (double)bc.om[r] + (double)bc.omlo[r];
     plan->wsum_all_lo = fall - (double)bc.wsum;
-    // mapping
+    // mapping and layouts
     const int ngroups = (d->nbins + 31) / 32;
     plan->ngroups = ngroups;
-    if (d->flags & 2) plan->mapping = MAP_SPLIT;
-    else if (d->flags & 4) plan->mapping = MAP_BINS;
+    if ((d->flags & GNA_PLAN_FORCE_SPLIT) && !plan->uniform)
+        return fail(plan, GNA_EINVAL, "the split mapping needs equal node counts for all points");
+    if (d->flags & GNA_PLAN_FORCE_SPLIT) plan->mapping = MAP_SPLIT;
+    else if (d->flags & GNA_PLAN_FORCE_BINS) plan->mapping = MAP_BINS;
     else if (plan->uniform && (plan->n_uniform >= 1024 || (int64_t)d->npts * ngroups < 16LL * plan->sm_count))
         plan->mapping = MAP_SPLIT;
     else plan->mapping = MAP_BINS;
-    if (plan->mapping == MAP_SPLIT && !plan->uniform)
-        return fail(plan, GNA_EINVAL, "the split mapping needs equal node counts for all points");
+    const bool forced = (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_BINS)) != 0;
+    const bool small = plan->uniform && (int64_t)d->nbins * plan->n_uniform <= (1LL << 20);
+    plan->has_split = plan->mapping == MAP_SPLIT || (!forced && small);
+    plan->has_bins = plan->mapping == MAP_BINS || (!forced && small);
     const bool shared = plan->uniform;
     plan->ngrids = shared ? 1 : d->npts;
-    const int nbins_pad = (plan->mapping == MAP_BINS) ? ngroups * 32 : d->nbins;
-    // grid offsets
+    const int nbins_pad = ngroups * 32;
+    // grid offsets of the bins layout (the split layout is one bin-major grid)
     std::vector<int64_t> goff(plan->ngrids);
     std::vector<int> gn(plan->ngrids);
     int64_t off = 0;
@@ -530,7 +539,9 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         gn[g] = plan->counts[g];
         off += (int64_t)nbins_pad * gn[g];
     }
-    plan->grid_len = off;
+    const int64_t len_bins = off;
+    const int64_t len_split = (int64_t)d->nbins * plan->n_uniform;
+    plan->grid_len = plan->has_bins ? len_bins : len_split;
     plan->total_nodes = 0;
     for (int g = 0; g < plan->ngrids; g++) plan->total_nodes += (int64_t)d->nbins * gn[g];
     const bool want64 = plan->ph == 2;
@@ -538,9 +549,15 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     if (want_plain && !plan->uniform) return fail(plan, GNA_EINVAL, "the plain chain needs equal node counts");
     TRY(dalloc(plan, &plan->d_edges, d->nbins + 1));
     CU(cudaMemcpyAsync(plan->d_edges, d->edges, sizeof(double) * (d->nbins + 1), cudaMemcpyHostToDevice, s));
-    if (plan->ph < 2) TRY(dalloc(plan, &plan->grid_ff, plan->grid_len));
-    if (want64) TRY(dalloc(plan, &plan->grid64, plan->grid_len));
-    const bool plain_alias = want_plain && want64 && plan->mapping == MAP_SPLIT;
+    if (plan->has_split) {
+        if (plan->ph < 2) TRY(dalloc(plan, &plan->grid_split, len_split));
+        if (want64) TRY(dalloc(plan, &plan->grid64_split, len_split));
+    }
+    if (plan->has_bins) {
+        if (plan->ph < 2) TRY(dalloc(plan, &plan->grid_bins, len_bins));
+        if (want64) TRY(dalloc(plan, &plan->grid64_bins, len_bins));
+    }
+    const bool plain_alias = want_plain && plan->grid64_split;
     if (want_plain && !plain_alias) TRY(dalloc(plan, &plan->plain64, (size_t)d->nbins * plan->n_uniform));
     TRY(dalloc(plan, &plan->d_goff, plan->ngrids));
     TRY(dalloc(plan, &plan->d_gn, plan->ngrids));
@@ -564,24 +581,34 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         go += n;
     }
     // energy grids
-    const int layout = (plan->mapping == MAP_BINS) ? 1 : 0;
-    for (int g = 0; g < plan->ngrids; g++) {
-        const int n = gn[g];
-        CU(launch_build_grid(d->nbins, nbins_pad, plan->d_edges, n, glx + gl_off[n], glw + gl_off[n], plan->e_scale,
-                             layout, plan->grid_ff ? plan->grid_ff + goff[g] : nullptr,
-                             plan->grid64 ? plan->grid64 + goff[g] : nullptr, (g == 0) ? plan->plain64 : nullptr, s));
+    if (plan->has_split) {
+        const int n = plan->n_uniform;
+        CU(launch_build_grid(d->nbins, d->nbins, plan->d_edges, n, glx + gl_off[n], glw + gl_off[n], plan->e_scale, 0,
+                             plan->grid_split, plan->grid64_split, plan->plain64, s));
     }
-    if (plain_alias) plan->plain64 = plan->grid64;
-    if (plan->grid_ff) {
+    if (plan->has_bins)
+        for (int g = 0; g < plan->ngrids; g++) {
+            const int n = gn[g];
+            CU(launch_build_grid(d->nbins, nbins_pad, plan->d_edges, n, glx + gl_off[n], glw + gl_off[n],
+                                 plan->e_scale, 1, plan->grid_bins ? plan->grid_bins + goff[g] : nullptr,
+                                 plan->grid64_bins ? plan->grid64_bins + goff[g] : nullptr,
+                                 (g == 0 && !plan->has_split) ? plan->plain64 : nullptr, s));
+        }
+    if (plain_alias) plan->plain64 = plan->grid64_split;
+    if (plan->ph < 2) {
         TRY(dalloc(plan, &plan->d_sumW, (size_t)plan->ngrids * d->nbins));
-        for (int g = 0; g < plan->ngrids; g++)
-            CU(launch_sum_weights(plan->grid_ff + goff[g], d->nbins, gn[g], layout, plan->d_sumW + (size_t)g * d->nbins, s));
+        for (int g = 0; g < plan->ngrids; g++) {
+            if (plan->has_split)
+                CU(launch_sum_weights(plan->grid_split, d->nbins, gn[g], 0, plan->d_sumW + (size_t)g * d->nbins, s));
+            else
+                CU(launch_sum_weights(plan->grid_bins + goff[g], d->nbins, gn[g], 1, plan->d_sumW + (size_t)g * d->nbins, s));
+        }
     }
     CU(cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&plan->ev_in, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&plan->ev_out, cudaEventDisableTiming));
     // task list (bins mapping): (point, group) ordered by decreasing node count
-    if (plan->mapping == MAP_BINS) {
+    if (plan->has_bins) {
         if ((int64_t)d->npts * ngroups >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many bin groups");
         std::vector<int> order(d->npts);
         for (int p = 0; p < d->npts; p++) order[p] = p;
@@ -594,12 +621,12 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         TRY(dalloc(plan, &plan->d_tasks, tasks.size()));
         CU(cudaMemcpyAsync(plan->d_tasks, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, s));
     }
-    plan->ncounters = 1 + (int64_t)d->npts + (plan->mapping == MAP_SPLIT ? (int64_t)d->npts * d->nbins : 0);
+    plan->ncounters = 1 + (int64_t)d->npts + (plan->has_split ? (int64_t)d->npts * d->nbins : 0);
     TRY(dalloc(plan, &plan->d_counters, plan->ncounters));
     // scratch
     TRY(dalloc(plan, &plan->d_pc, d->npts));
     const int nv_max = fused_nv(plan->nl_inst, true, true);
-    if (plan->mapping == MAP_SPLIT) {
+    if (plan->has_split) {
         // ranges are at least 128 nodes long, so a bin meets at most ceil(n / 128) + 1 of
         // them; the slot count is capped so that the partials stay within 256 M values
         const int64_t pairs = (int64_t)d->npts * d->nbins;
@@ -916,19 +943,28 @@ gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen) {
 
 gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     if (!plan || !text) return GNA_EINVAL;
-    int block = plan->block, npt = plan->npt, gm = plan->grid_mult;
+    int block = plan->block, npt = plan->npt, gm = plan->grid_mult, mapping = plan->mapping;
     const char* b = strstr(text, "block=");
     const char* n = strstr(text, "nodes=");
     const char* g = strstr(text, "grid=");
+    const char* m = strstr(text, "mapping=");
     if (b) block = atoi(b + 6);
     if (n) npt = atoi(n + 6);
     if (g) gm = atoi(g + 5);
+    if (m) {
+        if (!strncmp(m + 8, "split", 5)) mapping = MAP_SPLIT;
+        else if (!strncmp(m + 8, "bins", 4)) mapping = MAP_BINS;
+        else return fail(plan, GNA_EINVAL, "bad mapping in '%s'", text);
+    }
     if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64)
         return fail(plan, GNA_EINVAL, "bad tuning '%s'", text);
-    if (plan->mapping == MAP_SPLIT && npt < 4) return fail(plan, GNA_EINVAL, "nodes per lane must be >= 4");
+    if ((mapping == MAP_SPLIT && !plan->has_split) || (mapping == MAP_BINS && !plan->has_bins))
+        return fail(plan, GNA_EINVAL, "the plan has no grid for the %s mapping", mapping == MAP_SPLIT ? "split" : "bins");
+    if (mapping == MAP_SPLIT && npt < 4) return fail(plan, GNA_EINVAL, "nodes per lane must be >= 4");
     plan->block = block;
     plan->npt = npt;
     plan->grid_mult = gm;
+    plan->mapping = mapping;
     destroy_graph(plan);
     return GNA_OK;
 }
@@ -938,30 +974,35 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
     if (!plan || !params || !data) return GNA_EINVAL;
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool graph = plan->use_graph;
-    plan->use_graph = false;
-    std::vector<std::pair<int, int>> cand;
+    // candidates are timed the way the plan will run them (graph replay when
+    // the plan uses graphs: each candidate's first call captures its graph)
+    std::vector<std::string> cand;
     const int blocks[3] = {64, 128, 256};
-    if (plan->mapping == MAP_SPLIT) {
+    char t[96];
+    if (plan->has_split) {
         // block size only changes how the equal ranges sit on the SMs; the
         // minimum range length matters only for workloads smaller than the GPU
         const int npts_c[3] = {4, 16, 64};
         for (int b : blocks)
-            for (int m : npts_c) cand.push_back({b, m});
-    } else {
-        for (int b : blocks) cand.push_back({b, 1});
+            for (int m : npts_c) {
+                snprintf(t, sizeof(t), "mapping=split block=%d nodes=%d", b, m);
+                cand.push_back(t);
+            }
     }
-    const int old_block = plan->block, old_npt = plan->npt;
+    if (plan->has_bins)
+        for (int b : blocks) {
+            snprintf(t, sizeof(t), "mapping=bins block=%d nodes=1", b);
+            cand.push_back(t);
+        }
+    char best_t[128];
+    gna_plan_get_tuning(plan, best_t, sizeof(best_t));
     float best = 1e30f;
-    int bb = old_block, bm = old_npt;
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     gna_outputs o{plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr};
-    for (auto& c : cand) {
-        char t[64];
-        snprintf(t, sizeof(t), "block=%d nodes=%d", c.first, c.second);
-        if (gna_plan_set_tuning(plan, t) != GNA_OK) continue;
+    for (const std::string& c : cand) {
+        if (gna_plan_set_tuning(plan, c.c_str()) != GNA_OK) continue;
         gna_status st = gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);  // warm-up
         if (st != GNA_OK) continue;
         cudaEventRecord(e0, s);
@@ -972,16 +1013,12 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            bb = c.first;
-            bm = c.second;
+            snprintf(best_t, sizeof(best_t), "%s", c.c_str());
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    plan->use_graph = graph;
-    char t[64];
-    snprintf(t, sizeof(t), "block=%d nodes=%d", bb, bm);
-    gna_status st = gna_plan_set_tuning(plan, t);
+    gna_status st = gna_plan_set_tuning(plan, best_t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "autotune: %s", cudaGetErrorString(e));
     return st;

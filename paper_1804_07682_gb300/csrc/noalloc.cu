@@ -34,7 +34,7 @@ constexpr size_t kOffCnt = align256(kOffPc + sizeof(PointConst));
 constexpr size_t kOffSumW = align256(kOffCnt + sizeof(int) * (2 + kMaxBins));
 constexpr size_t kOffPart = align256(kOffSumW + sizeof(double) * kMaxBins);
 constexpr size_t kOffBin = align256(kOffPart + sizeof(float2) * kMaxTiles * kNVT);
-constexpr size_t kScratchBytes = align256(kOffBin + sizeof(double) * kMaxBins * 5);
+constexpr size_t kScratchBytes = align256(kOffBin + sizeof(float2) * kMaxBins * 5);
 static_assert(kScratchBytes < (1u << 20), "scratch must stay below 1 MiB");
 
 }  // namespace
@@ -227,7 +227,7 @@ extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, 
     ea.kind = kind;
     ea.data = data;
     ea.mu_out = mu;
-    ea.binvals = reinterpret_cast<double*>(base + kOffBin);
+    ea.binvals = reinterpret_cast<float2*>(base + kOffBin);
     ea.NBV = 5;
     ea.sumW = a.sumW;
     ea.shared_grid = 1;

@@ -205,6 +205,40 @@ def test_autotune_keeps_parity(api):
     assert rel(out["chi2"][0].item(), ref["chi2"]) < 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_mapping_is_a_tuning_choice_on_small_grids(api, prec):
+    # a small uniform grid keeps both layouts: the two mappings give the same
+    # answer from one plan, and the autotuner (timing graph replays) may pick either
+    case = get_case("reactor_200x50")
+    w = case.w
+    plan = make_plan(api, case, prec)
+    p = plan.params_tensor(w.theta)
+    d = dev(case.data)
+    ref = case.oracle_point(0)
+    tol = TOL[prec]
+    res = {}
+    for m in ("split", "bins"):
+        plan.tuning = f"mapping={m} block=128 nodes=4"
+        assert plan.tuning.startswith(f"mapping={m}")
+        out = plan.eval(p, d, grad=True, mu=True)
+        assert abs(out["chi2"][0].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, case.data, w.kind)
+        assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < tol
+        res[m] = out["chi2"][0].item()
+    assert rel(res["split"], res["bins"]) < 2 * tol
+    plan.set_graph(True)
+    text = plan.autotune(p, d, reps=5)
+    assert text.startswith("mapping=")
+    out = plan.eval(p, d, grad=True)
+    assert abs(out["chi2"][0].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, case.data, w.kind)
+    plan.close()
+    # a plan whose mapping was forced keeps one layout only
+    forced = make_plan(api, case, prec, "split")
+    from paper_1804_07682_gb300 import _native as N
+    with pytest.raises(N.GnaError):
+        forced.tuning = "mapping=bins"
+    forced.close()
+
+
 def test_autograd_function(api):
     case = get_case("nuisance_64x1000")
     w = case.w

@@ -40,8 +40,8 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     """Algorithmic FP32 operations (FMA = 1) of the fused kernel per energy node.
 
     Per (node, baseline): double-float phase and reduction mod pi 2 x 10,
-    sin/cos polynomials 2 x 12 (u = r^2, degree-11 sine, degree-10 cosine),
-    angle addition 2, three squares, three weighted sums (44 + 2 + 3 + 3 = 52);
+    sin/cos polynomials 2 x 10 (u = r^2, degree-9 sine 5, degree-8 cosine 4),
+    angle addition 2, three squares, three weighted sums (40 + 2 + 3 + 3 = 48);
     with one or more baselines and no per-baseline sums the weights enter as
     hi + lo (3 more); gradient: cos of the sum 2, three sin*cos products and
     three weighted sums (8); spectra: P_r 3 + Kahan product-sum 4 (7).  Per
@@ -50,7 +50,7 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     product-sums 16.
     """
     omlo = nL > 1 and not spec
-    per_r = 52 + (3 if omlo else 0) + (8 if grad else 0) + (7 if spec else 0)
+    per_r = 48 + (3 if omlo else 0) + (8 if grad else 0) + (7 if spec else 0)
     per_node = 11 + (3 if omlo else 0) + (26 if grad else 0)
     return nL * per_r + per_node
 

@@ -115,27 +115,39 @@ __device__ __forceinline__ void warp_transpose_reduce(float2 (&v)[NVP], int lane
 
 // ----------------------------------------- phase reduction and sin / cos --
 // sin r and cos r on |r| <= pi/2 (+ margin), FP32 polynomials (ff_consts.h).
-__device__ __forceinline__ void sincos_poly(float r, float& s, float& c) {
-    float u = __fmul_rn(r, r);
+// Horner tails S1 + u (S2 + ...) and C1 + u (C2 + ...); the generated
+// header defines four or five coefficients of each.
+__device__ __forceinline__ float sin_tail(float u) {
+#if defined(GNA_SIN_C5)
     float ps = fmaf(GNA_SIN_C5, u, GNA_SIN_C4);
+#else
+    float ps = GNA_SIN_C4;
+#endif
     ps = fmaf(ps, u, GNA_SIN_C3);
     ps = fmaf(ps, u, GNA_SIN_C2);
-    ps = fmaf(ps, u, GNA_SIN_C1);
-    s = fmaf(__fmul_rn(r, u), ps, r);
+    return fmaf(ps, u, GNA_SIN_C1);
+}
+
+__device__ __forceinline__ float cos_tail(float u) {
+#if defined(GNA_COS_C5)
     float pc = fmaf(GNA_COS_C5, u, GNA_COS_C4);
+#else
+    float pc = GNA_COS_C4;
+#endif
     pc = fmaf(pc, u, GNA_COS_C3);
     pc = fmaf(pc, u, GNA_COS_C2);
-    pc = fmaf(pc, u, GNA_COS_C1);
-    c = fmaf(u, pc, 1.0f);
+    return fmaf(pc, u, GNA_COS_C1);
+}
+
+__device__ __forceinline__ void sincos_poly(float r, float& s, float& c) {
+    float u = __fmul_rn(r, r);
+    s = fmaf(__fmul_rn(r, u), sin_tail(u), r);
+    c = fmaf(u, cos_tail(u), 1.0f);
 }
 
 __device__ __forceinline__ float sin_poly(float r) {
     float u = __fmul_rn(r, r);
-    float ps = fmaf(GNA_SIN_C5, u, GNA_SIN_C4);
-    ps = fmaf(ps, u, GNA_SIN_C3);
-    ps = fmaf(ps, u, GNA_SIN_C2);
-    ps = fmaf(ps, u, GNA_SIN_C1);
-    return fmaf(__fmul_rn(r, u), ps, r);
+    return fmaf(__fmul_rn(r, u), sin_tail(u), r);
 }
 
 // 1.5 * 2^23: adding it rounds a float of magnitude < 2^22 to an integer.

@@ -159,8 +159,21 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
 __device__ inline void point_reduce(const EpiArgs& a, int p, int w, int nw, int lane) {
     const float2* bv = a.binvals + (int64_t)p * a.nbins * a.NBV;
     for (int v = w; v < a.NBV; v += nw) {
+        // a lane's bins i = lane, lane + 32, ... in order; the loads are issued
+        // eight at a time so that the L2 latency is paid once per eight bins
+        // (this reduction is the kernel's tail: every other warp has finished)
         float2 s = make_float2(0.f, 0.f);
-        for (int i = lane; i < a.nbins; i += 32) s = ff_add(s, __ldcg(bv + (int64_t)i * a.NBV + v));
+        for (int i0 = lane; i0 < a.nbins; i0 += 8 * 32) {
+            float2 t[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int i = i0 + 32 * j;
+                t[j] = (i < a.nbins) ? __ldcg(bv + (int64_t)i * a.NBV + v) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (i0 + 32 * j < a.nbins) s = ff_add(s, t[j]);
+        }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) s = ff_add(s, shfl_xor_f2(s, o));
         if (lane == 0) {

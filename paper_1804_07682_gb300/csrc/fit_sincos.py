@@ -18,8 +18,8 @@ from fractions import Fraction
 import numpy as np
 
 R_MAX = math.pi / 2 + 2e-3
-N_SIN = 5  # S1..S5: odd degree 11
-N_COS = 5  # C1..C5: even degree 10
+N_SIN = 4  # S1..S4: odd degree 9 (error ~5e-9)
+N_COS = 4  # C1..C4: even degree 8 (error ~5e-8)
 
 # pi to 60 digits (textbook value)
 PI = Fraction("3.14159265358979323846264338327950288419716939937510582097494")

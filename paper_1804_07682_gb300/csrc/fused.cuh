@@ -153,7 +153,7 @@ __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v
 // all points is cut into equal contiguous ranges, one per resident warp
 // (range length `per`).  A warp walks its range: lane l takes nodes f + l,
 // f + l + 32, ... (bin-major grid, node f at f mod (nbins n): every warp load is
-// 512 contiguous bytes, the next one prefetched while the current node is
+// 512 contiguous bytes, the next two prefetched while the current node is
 // computed, across bin boundaries too).  At each bin boundary the warp reduces
 // its Kahan sums with a transposed shuffle reduction and stores the segment's
 // partial in slot w - w_first(bin); the warp storing a bin's last segment sums
@@ -165,6 +165,7 @@ struct SplitArgs {
     int nbins, n, npts;
     int64_t per;    // nodes per warp range
     int maxseg;     // partial slots per (point, bin)
+    int gstep;      // 32 mod (nbins n): a lane's step through the grid
     const PointConst* pcs;
     BaseConst bc;
     float2* part;   // [npts][nbins][maxseg][NV]
@@ -190,8 +191,14 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
     int last_p = -1;
     M m;
     int64_t f = f0 + lane;
-    int64_t gi = (f < f1) ? f % gn : 0;  // grid index of f, advanced with at most one wrap per step
-    float4 cur = (f < f1) ? __ldg(a.grid + gi) : make_float4(1.f, 0.f, 0.f, 0.f);
+    // two nodes in flight per lane (f + 32 and f + 64 while f is computed): one
+    // was too few to cover the load latency at 4 warps per scheduler.  Grid
+    // indices are taken mod gn, so loads past the range end stay in bounds.
+    int64_t gi = f % gn;
+    float4 cur = __ldg(a.grid + gi);
+    gi += a.gstep;  // gi + 32 mod gn, with gi, gstep < gn
+    if (gi >= gn) gi -= gn;
+    float4 nx1 = __ldg(a.grid + gi);  // gi: grid index of f + 32
     for (int64_t pos = f0; pos < f1;) {
         const int64_t q = pos / a.n;  // (point, bin) pair
         const int p = (int)(q / a.nbins);
@@ -205,13 +212,13 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
 #pragma unroll
         for (int v = 0; v < NV; v++) kzero(acc[v]);
         while (f < seg_end) {
-            const int64_t fn = f + 32;
-            int64_t gin = gi + 32;
+            int64_t gin = gi + a.gstep;
             if (gin >= gn) gin -= gn;
-            const float4 nxt = (fn < f1) ? __ldg(a.grid + gin) : cur;
+            const float4 nx2 = __ldg(a.grid + gin);  // node f + 64
             m.update(cur, acc);
-            cur = nxt;
-            f = fn;
+            cur = nx1;
+            nx1 = nx2;
+            f += 32;
             gi = gin;
         }
         // lanes whose next node lies past this segment wait here with f >= seg_end

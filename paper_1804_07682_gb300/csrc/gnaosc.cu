@@ -327,7 +327,8 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
     if (plan->mapping == MAP_SPLIT) {
         if (plan->ph < 2) {
-            SplitArgs a{plan->grid_split, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg,
+            const int gstep = (int)(32 % ((int64_t)plan->nbins * plan->n_uniform));
+            SplitArgs a{plan->grid_split, plan->nbins, plan->n_uniform, plan->npts, sh.per, sh.maxseg, gstep,
                         plan->d_pc, plan->bc, (float2*)plan->d_part, ea};
             CU(dispatch_split(plan->ph, plan->nl_inst, grad, spec, &a, sh.grid, plan->block, s));
         } else {

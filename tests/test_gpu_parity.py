@@ -160,6 +160,19 @@ def test_chain_degenerate_shapes(api):
         check_chain(api, case2, prec)
 
 
+@pytest.mark.parametrize("mapping", ["split", "bins"])
+@pytest.mark.parametrize("nbins,n,npts", [(1, 8, 40), (3, 5, 50), (2, 16, 3), (7, 3, 33)])
+def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):
+    # the whole grid (bins x nodes) has fewer nodes than a warp has lanes, so a
+    # lane's next node lies several bins, or several points, further on
+    rng = np.random.default_rng(nbins * 100 + n)
+    theta = np.tile(np.array(wl.TRUTH), (npts, 1)) * rng.uniform(0.9, 1.1, size=(npts, 4))
+    w = wl.Workload("tiny", np.linspace(2.0, 8.0, nbins + 1), n, np.array([52.5, 53.0]), theta, wl.POISSON)
+    case = Case(w)
+    for prec in ("fp64", "ff"):
+        check_chain(api, case, prec, mapping)
+
+
 def test_plain_chain_matches_oracle(api):
     case = get_case("reactor8_40x3000")
     w = case.w

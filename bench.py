@@ -39,9 +39,10 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     """Algorithmic FP32 operations (FMA = 1) of the fused kernel per energy node.
 
-    Per (node, baseline): double-float phase and reduction mod pi 2 x 10,
-    sin/cos polynomials 2 x 10 (u = r^2, degree-9 sine 5, degree-8 cosine 4),
-    angle addition 2, three squares, three weighted sums (40 + 2 + 3 + 3 = 48);
+    Per (node, baseline): double-float phase and two-part reduction mod pi
+    2 x 9, sin/cos polynomials 2 x 10 (u = r^2, degree-9 sine 5, degree-8
+    cosine 4), angle addition 2, three squares, three weighted sums
+    (38 + 2 + 3 + 3 = 46);
     with one or more baselines and no per-baseline sums the weights enter as
     hi + lo (3 more); gradient: cos of the sum 2, three sin*cos products and
     three weighted sums (8); spectra: P_r 3 + Kahan product-sum 4 (7).  Per
@@ -50,7 +51,7 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     product-sums 16.
     """
     omlo = nL > 1 and not spec
-    per_r = 48 + (3 if omlo else 0) + (8 if grad else 0) + (7 if spec else 0)
+    per_r = 46 + (3 if omlo else 0) + (8 if grad else 0) + (7 if spec else 0)
     per_node = 11 + (3 if omlo else 0) + (26 if grad else 0)
     return nL * per_r + per_node
 

@@ -156,15 +156,17 @@ __device__ __forceinline__ float sin_poly(float r) {
 // Phase c * e with c = ch + cl and e = eh + el (double-float), reduced modulo
 // pi: returns r with phase = q pi + r, |r| <= pi/2 (+ rounding), valid for
 // phase < 2^12 pi.  The product hi part is exact through the FMA residual;
-// q PI_A and q PI_B are exact (12-bit parts of pi, integer q < 2^12).
+// q PI_A is exact (12-bit PI_A, integer q < 2^12) and the FMA with PI_B2
+// rounds once; PI_A + PI_B2 misses pi by GNA_PI_E2 (5e-12), so the reduction
+// adds at most q * 5e-12 (2e-8 rad at the largest phase) to the float
+// rounding of r.
 __device__ __forceinline__ float reduce_pi_ff(float ch, float cl, float eh, float el) {
     float p = __fmul_rn(ch, eh);
     float e = __fmaf_rn(ch, eh, -p);
     float lo = __fmaf_rn(ch, el, __fmaf_rn(cl, eh, e));
     float q = __fsub_rn(__fmaf_rn(p, GNA_INV_PI_F, GNA_ROUND_MAGIC), GNA_ROUND_MAGIC);
     float r = __fmaf_rn(-q, GNA_PI_A, p);
-    r = __fmaf_rn(-q, GNA_PI_B, r);
-    r = __fmaf_rn(-q, GNA_PI_C, r);
+    r = __fmaf_rn(-q, GNA_PI_B2, r);
     return __fadd_rn(r, lo);
 }
 

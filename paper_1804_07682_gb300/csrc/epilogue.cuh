@@ -45,8 +45,11 @@ struct EpiArgs {
     double* chi2;          // [npts]
     double* grad;          // [npts][4] or NULL
     double* H;             // [npts][10] or NULL
-    int* pt_cnt;           // [npts] bins finished, zeroed before the launch
-    int* bin_cnt;          // [npts][nbins] chunks finished (split mapping), zeroed before the launch
+    float2* gvals;         // [npts][ngroups][NBV] sums over groups of 32 bins
+    int ngroups;           // ceil(nbins / 32)
+    int* pt_cnt;           // [npts] groups finished, zeroed before the launch
+    int* grp_cnt;          // [npts][ngroups] bins finished, zeroed before the launch
+    int* bin_cnt;          // [npts][nbins] segments finished (split mapping), zeroed before the launch
 };
 
 __device__ __forceinline__ float2 to_ff(double x) {
@@ -152,40 +155,81 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
         for (int r = 0; r < a.nL_out; r++) a.spectra_out[((int64_t)p * a.nL_out + r) * a.nbins + i] = v[off + r];
 }
 
-// Warps w = 0..nw-1 of the caller sum the per-bin values of point p (value v
-// by warp v mod nw; lane l takes bins l, l+32, ...; xor butterfly, all in
-// double-float) and write the point's outputs.  Reads go through L2
-// (__ldcg): other SMs wrote them.
-__device__ inline void point_reduce(const EpiArgs& a, int p, int w, int nw, int lane) {
-    const float2* bv = a.binvals + (int64_t)p * a.nbins * a.NBV;
-    for (int v = w; v < a.NBV; v += nw) {
-        // a lane's bins i = lane, lane + 32, ... in order; the loads are issued
-        // eight at a time so that the L2 latency is paid once per eight bins
-        // (this reduction is the kernel's tail: every other warp has finished)
-        float2 s = make_float2(0.f, 0.f);
-        for (int i0 = lane; i0 < a.nbins; i0 += 8 * 32) {
-            float2 t[8];
+// The per-bin values are summed in two levels, each one warp-wide reduction
+// in a fixed order (so the result does not depend on which warp finished
+// what): the warp that finishes the last bin of a group of 32 bins sums the
+// group, and the warp that finishes the last group of a point sums the
+// groups and writes the point's outputs.  At the end of a launch this leaves
+// two short reductions after the last bin instead of one over all bins.
+// Reads go through L2 (__ldcg): other SMs wrote the values.
+
+// Group g of point p: lane l takes bin 32 g + l; lanes of the group whose
+// sum is stored hold value lane / 2 after the transposed reduction.
+__device__ inline void group_reduce(const EpiArgs& a, int p, int g, int lane) {
+    const int i = (g << 5) + lane;
+    const float2* bv = a.binvals + ((int64_t)p * a.nbins + i) * a.NBV;
+    float2 v[16];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int i = i0 + 32 * j;
-                t[j] = (i < a.nbins) ? __ldcg(bv + (int64_t)i * a.NBV + v) : make_float2(0.f, 0.f);
-            }
+    for (int j = 0; j < 16; j++) v[j] = (j < a.NBV && i < a.nbins) ? __ldcg(bv + j) : make_float2(0.f, 0.f);
+    warp_transpose_reduce<16>(v, lane);
+    const int vi = lane >> 1;
+    if ((lane & 1) == 0 && vi < a.NBV) a.gvals[((int64_t)p * a.ngroups + g) * a.NBV + vi] = v[0];
+}
+
+// Point p: lane l sums groups l, l + 32, ... in order, then one transposed
+// reduction over the lanes; the point's outputs are written.
+__device__ inline void point_reduce(const EpiArgs& a, int p, int lane) {
+    float2 v[16];
 #pragma unroll
-            for (int j = 0; j < 8; j++)
-                if (i0 + 32 * j < a.nbins) s = ff_add(s, t[j]);
-        }
+    for (int j = 0; j < 16; j++) v[j] = make_float2(0.f, 0.f);
+    for (int g = lane; g < a.ngroups; g += 32) {
+        const float2* gv = a.gvals + ((int64_t)p * a.ngroups + g) * a.NBV;
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) s = ff_add(s, shfl_xor_f2(s, o));
-        if (lane == 0) {
-            const double tot = (double)s.x + (double)s.y;
-            if (v == 0) a.chi2[p] = tot;
-            else if (v < 5) {
-                if (a.grad) a.grad[(int64_t)p * 4 + v - 1] = tot;
-            } else if (a.H) {
-                a.H[(int64_t)p * 10 + v - 5] = tot;
-            }
+        for (int j = 0; j < 15; j++)
+            if (j < a.NBV) v[j] = ff_add(v[j], __ldcg(gv + j));
+    }
+    warp_transpose_reduce<16>(v, lane);
+    const int vi = lane >> 1;
+    if ((lane & 1) == 0 && vi < a.NBV) {
+        const double tot = (double)v[0].x + (double)v[0].y;
+        if (vi == 0) a.chi2[p] = tot;
+        else if (vi < 5) {
+            if (a.grad) a.grad[(int64_t)p * 4 + vi - 1] = tot;
+        } else if (a.H) {
+            a.H[(int64_t)p * 10 + vi - 5] = tot;
         }
     }
+}
+
+// The whole group g of point p has its per-bin values stored (whole warp
+// calls).  Not inlined: its registers stay out of the node loops' allocation.
+static __device__ __noinline__ void group_done(const EpiArgs& a, int p, int g, int lane) {
+    __threadfence();
+    __syncwarp();
+    group_reduce(a, p, g, lane);
+    int lastp = 0;
+    if (lane == 0) {
+        __threadfence();
+        lastp = (atomicAdd(a.pt_cnt + p, 1) == a.ngroups - 1);
+    }
+    lastp = __shfl_sync(0xffffffffu, lastp, 0);
+    if (lastp) {
+        __threadfence();
+        point_reduce(a, p, lane);
+    }
+}
+
+// Bin i of point p has its per-bin values stored by lane 0 (whole warp calls).
+__device__ inline void bin_done(const EpiArgs& a, int p, int i, int lane) {
+    const int g = i >> 5;
+    const int gsize = min(32, a.nbins - (g << 5));
+    int lastg = 0;
+    if (lane == 0) {
+        __threadfence();
+        lastg = (atomicAdd(a.grp_cnt + (int64_t)p * a.ngroups + g, 1) == gsize - 1);
+    }
+    lastg = __shfl_sync(0xffffffffu, lastg, 0);
+    if (lastg) group_done(a, p, g, lane);
 }
 
 }  // namespace gna

@@ -15,6 +15,9 @@
 #define GNA_PI_A (3.140625f)
 #define GNA_PI_B (0.00096750259399414062f)
 #define GNA_PI_C (1.509958025e-07f)
+// pi = PI_A + PI_B2 + e2 with PI_B2 the float32 rounding of pi - PI_A, |e2| = 5.13e-12.
+#define GNA_PI_B2 (9.676535847e-04f)
+#define GNA_PI_E2 (5.127e-12)
 #define GNA_INV_PI_F (3.183098733e-01f)
 // pi = PI_DA + PI_DB + PI_DC in double; PI_DA, PI_DB have 26 significant bits.
 #define GNA_PI_DA (3.1415926218032837)

@@ -138,6 +138,12 @@ def main():
     out.write("#define GNA_PI_A (%.17gf)\n" % A)
     out.write("#define GNA_PI_B (%.17gf)\n" % B)
     out.write("#define GNA_PI_C (%.9ef)\n" % C)
+    # two-part split for the fused kernels: PI_B2 = float32(pi - PI_A)
+    B2 = float(np.float32(float(PI - Fraction(A))))
+    err2 = abs(float(PI - Fraction(A) - Fraction(B2)))
+    out.write("// pi = PI_A + PI_B2 + e2 with PI_B2 the float32 rounding of pi - PI_A, |e2| = %.2e.\n" % err2)
+    out.write("#define GNA_PI_B2 (%.9ef)\n" % B2)
+    out.write("#define GNA_PI_E2 (%.3e)\n" % err2)
     out.write("#define GNA_INV_PI_F (%.9ef)\n" % float(np.float32(1 / math.pi)))
     # double-precision split for the FP64-phase variant: 26 + 26 bits + rest
     def top_bits(x, bits):

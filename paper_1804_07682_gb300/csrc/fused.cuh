@@ -244,24 +244,24 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
             __threadfence();
             double val = 0.0;
             if (lane < NV) {
-                float2 sum = __ldcg(pp + lane);
-                for (int sg = 1; sg < nseg; sg++) sum = ff_add(sum, __ldcg(pp + sg * NV + lane));
+                // slots in order; loads issued eight at a time
+                float2 sum = make_float2(0.f, 0.f);
+                for (int s0 = 0; s0 < nseg; s0 += 8) {
+                    float2 t[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        t[j] = (s0 + j < nseg) ? __ldcg(pp + (s0 + j) * NV + lane) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (s0 + j < nseg) sum = ff_add(sum, t[j]);
+                }
                 val = (double)sum.x + (double)sum.y;
             }
             double sv[NV];
 #pragma unroll
             for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
-            int lastp = 0;
-            if (lane == 0) {
-                bin_epilogue(a.ea, p, i, sv);
-                __threadfence();
-                lastp = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
-            }
-            lastp = __shfl_sync(0xffffffffu, lastp, 0);
-            if (lastp) {
-                __threadfence();
-                point_reduce(a.ea, p, 0, 1, lane);
-            }
+            if (lane == 0) bin_epilogue(a.ea, p, i, sv);
+            bin_done(a.ea, p, i, lane);
         }
         pos = seg_end;
     }
@@ -337,16 +337,8 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
 #pragma unroll
             for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
             bin_epilogue(a.ea, p, i, v);
-            __threadfence();
         }
-        __syncwarp();
-        int last = 0;
-        if (lane == 0) last = (atomicAdd(a.ea.pt_cnt + p, 1) == a.ngroups - 1);
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-            __threadfence();
-            point_reduce(a.ea, p, 0, 1, lane);
-        }
+        group_done(a.ea, p, b, lane);
     }
 }
 

@@ -128,17 +128,8 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
             double sv[NV];
 #pragma unroll
             for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
-            int lastp = 0;
-            if (lane == 0) {
-                bin_epilogue(a.ea, p, i, sv);
-                __threadfence();
-                lastp = (atomicAdd(a.ea.pt_cnt + p, 1) == a.nbins - 1);
-            }
-            lastp = __shfl_sync(0xffffffffu, lastp, 0);
-            if (lastp) {
-                __threadfence();
-                point_reduce(a.ea, p, 0, 1, lane);
-            }
+            if (lane == 0) bin_epilogue(a.ea, p, i, sv);
+            bin_done(a.ea, p, i, lane);
         }
         pos = seg_end;
     }
@@ -186,16 +177,8 @@ __global__ void __launch_bounds__(256) k_fused64_bins(BinArgs64 a) {
         const int i = b * 32 + lane;
         if (i < a.nbins) {
             bin_epilogue(a.ea, p, i, acc);
-            __threadfence();
         }
-        __syncwarp();
-        int last = 0;
-        if (lane == 0) last = (atomicAdd(a.ea.pt_cnt + p, 1) == a.ngroups - 1);
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-            __threadfence();
-            point_reduce(a.ea, p, 0, 1, lane);
-        }
+        group_done(a.ea, p, b, lane);
     }
 }
 

@@ -103,7 +103,9 @@ struct gna_plan {
     int ngrids = 0, ngroups = 0;
     int* d_tasks = nullptr;
     int ntasks = 0;
-    int* d_counters = nullptr;  // [1 + npts + npts*nbins (split)]: work counter, per-point, per-bin arrivals
+    // [1 + npts + npts*ngroups (+ npts*nbins, split)]: work counter, groups
+    // finished per point, bins finished per group, segments finished per bin
+    int* d_counters = nullptr;
     int64_t ncounters = 0;
     int maxseg_cap = 2;  // split mapping: partial slots per (point, bin) the plan allocated
     double* d_edges = nullptr;
@@ -114,6 +116,7 @@ struct gna_plan {
     void* d_part = nullptr;
     size_t part_cap = 0;  // elements of 8 bytes
     float2* d_binvals = nullptr;
+    float2* d_gvals = nullptr;  // [npts][ngroups][15] group sums
     double* d_H = nullptr;
     double* d_chi2_tmp = nullptr;
     double* d_grad_tmp = nullptr;
@@ -287,7 +290,9 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
                         (long long)plan->npts * plan->nbins * sh.maxseg * NV, plan->part_cap);
     }
     // work counter, per-point and per-bin arrival counters: one memset
-    CU(cudaMemsetAsync(plan->d_counters, 0, sizeof(int) * plan->ncounters, s));
+    const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups) +
+                         (plan->mapping == MAP_SPLIT ? (int64_t)plan->npts * plan->nbins : 0);
+    CU(cudaMemsetAsync(plan->d_counters, 0, sizeof(int) * ncnt, s));
     CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s));
     nl++;
     EpiArgs ea{};
@@ -319,8 +324,11 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     ea.chi2 = q.chi2;
     ea.grad = q.grad;
     ea.H = q.H;
+    ea.gvals = plan->d_gvals;
+    ea.ngroups = plan->ngroups;
     ea.pt_cnt = plan->d_counters + 1;
-    ea.bin_cnt = plan->d_counters + 1 + plan->npts;
+    ea.grp_cnt = plan->d_counters + 1 + plan->npts;
+    ea.bin_cnt = plan->d_counters + 1 + plan->npts + (int64_t)plan->npts * plan->ngroups;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(s, &cap));
     const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
@@ -525,7 +533,8 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         plan->mapping = MAP_SPLIT;
     else plan->mapping = MAP_BINS;
     const bool forced = (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_BINS)) != 0;
-    const bool small = plan->uniform && (int64_t)d->nbins * plan->n_uniform <= (1LL << 20);
+    const bool small = plan->uniform && (int64_t)d->nbins * plan->n_uniform <= (1LL << 20) &&
+                       (int64_t)d->npts * d->nbins <= (1LL << 16);
     plan->has_split = plan->mapping == MAP_SPLIT || (!forced && small);
     plan->has_bins = plan->mapping == MAP_BINS || (!forced && small);
     const bool shared = plan->uniform;
@@ -622,7 +631,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         TRY(dalloc(plan, &plan->d_tasks, tasks.size()));
         CU(cudaMemcpyAsync(plan->d_tasks, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, s));
     }
-    plan->ncounters = 1 + (int64_t)d->npts + (plan->has_split ? (int64_t)d->npts * d->nbins : 0);
+    plan->ncounters = 1 + (int64_t)d->npts * (1 + ngroups) + (plan->has_split ? (int64_t)d->npts * d->nbins : 0);
     TRY(dalloc(plan, &plan->d_counters, plan->ncounters));
     // scratch
     TRY(dalloc(plan, &plan->d_pc, d->npts));
@@ -638,6 +647,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
     }
     TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
+    TRY(dalloc(plan, &plan->d_gvals, (size_t)d->npts * ngroups * 15));
     TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
     TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
     TRY(dalloc(plan, &plan->d_grad_tmp, (size_t)d->npts * 4));

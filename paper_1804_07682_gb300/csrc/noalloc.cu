@@ -22,6 +22,7 @@ namespace {
 
 // Limits of the allocation-free evaluation.
 constexpr int kMaxBins = 2048;
+constexpr int kMaxGroups = kMaxBins / 32;
 constexpr int kMaxTiles = 16384;  // warp tiles of kTileNodes nodes over all bins
 constexpr int kTileNodes = 1024;  // 32 lanes x 32 nodes
 constexpr int kMaxNL = 8;
@@ -31,10 +32,11 @@ constexpr int kNVT = 6;  // combined prediction, four tangents, sum of the FP32 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffPc = 0;
 constexpr size_t kOffCnt = align256(kOffPc + sizeof(PointConst));
-constexpr size_t kOffSumW = align256(kOffCnt + sizeof(int) * (2 + kMaxBins));
+constexpr size_t kOffSumW = align256(kOffCnt + sizeof(int) * (2 + kMaxGroups + kMaxBins));
 constexpr size_t kOffPart = align256(kOffSumW + sizeof(double) * kMaxBins);
 constexpr size_t kOffBin = align256(kOffPart + sizeof(float2) * kMaxTiles * kNVT);
-constexpr size_t kScratchBytes = align256(kOffBin + sizeof(float2) * kMaxBins * 5);
+constexpr size_t kOffGrp = align256(kOffBin + sizeof(float2) * kMaxBins * 5);
+constexpr size_t kScratchBytes = align256(kOffGrp + sizeof(float2) * kMaxGroups * 5);
 static_assert(kScratchBytes < (1u << 20), "scratch must stay below 1 MiB");
 
 }  // namespace
@@ -54,7 +56,8 @@ struct NoAllocArgs {
     int nbins, n, nchunks;
     const PointConst* pc;
     BaseConst bc;
-    int* counters;  // [0] tile counter, [1] bins finished, [2 + i] chunks of bin i finished
+    int* counters;  // [0] tile counter, [1] groups finished, [2 + g] bins of group g finished,
+                    // [2 + kMaxGroups + i] chunks of bin i finished
     float2* part;   // [nbins][nchunks][kNVT]
     double* sumW;   // [nbins]
     gna::EpiArgs ea;
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(256, 2) k_noalloc_chi2(NoAllocArgs a) {
         }
         __syncwarp();
         int last = 0;
-        if (lane == 0) last = (atomicAdd(a.counters + 2 + i, 1) == a.nchunks - 1);
+        if (lane == 0) last = (atomicAdd(a.counters + 2 + kMaxGroups + i, 1) == a.nchunks - 1);
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last) {
             __threadfence();
@@ -124,18 +127,11 @@ __global__ void __launch_bounds__(256, 2) k_noalloc_chi2(NoAllocArgs a) {
             double sv[kNVT];
 #pragma unroll
             for (int j = 0; j < kNVT; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
-            int lastp = 0;
             if (lane == 0) {
                 a.sumW[i] = sv[NV];
                 gna::bin_epilogue(a.ea, 0, i, sv);
-                __threadfence();
-                lastp = (atomicAdd(a.counters + 1, 1) == a.nbins - 1);
             }
-            lastp = __shfl_sync(0xffffffffu, lastp, 0);
-            if (lastp) {
-                __threadfence();
-                gna::point_reduce(a.ea, 0, 0, 1, lane);
-            }
+            gna::bin_done(a.ea, 0, i, lane);
         }
     }
 }
@@ -234,11 +230,14 @@ extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, 
     ea.wsum_lo = (nl_inst == 1) ? bc.wsum_lo : fall - (double)bc.wsum;
     ea.chi2 = chi2;
     ea.grad = grad;
+    ea.gvals = reinterpret_cast<float2*>(base + kOffGrp);
+    ea.ngroups = (nbins + 31) / 32;
     ea.pt_cnt = a.counters + 1;
-    ea.bin_cnt = a.counters + 2;
+    ea.grp_cnt = a.counters + 2;
+    ea.bin_cnt = a.counters + 2 + kMaxGroups;
 
     // the counters are the only scratch that must start at zero
-    e = cudaMemsetAsync(a.counters, 0, sizeof(int) * (2 + nbins), s);
+    e = cudaMemsetAsync(a.counters, 0, sizeof(int) * (2 + kMaxGroups + nbins), s);
     if (e == cudaSuccess) e = gna::launch_prepare(params, 1, bc, reinterpret_cast<PointConst*>(base + kOffPc), s);
     if (e == cudaSuccess) {
         int dev = 0, sms = 0;

@@ -135,7 +135,8 @@ def test_chain_both_mappings(api, name, mapping):
     check_chain(api, get_case(name), "ff", mapping)
 
 
-@pytest.mark.parametrize("tuning", ["block=64 nodes=4", "block=128 nodes=7", "block=256 nodes=64", "block=96 nodes=5"])
+@pytest.mark.parametrize("tuning", ["block=64 nodes=4", "block=128 nodes=7", "block=256 nodes=64", "block=96 nodes=5",
+                                    "block=256 nodes=1024", "block=32 nodes=4 grid=1"])
 def test_chain_launch_shapes(api, tuning):
     case = get_case("reactor8_40x3000")
     w = case.w
@@ -145,6 +146,22 @@ def test_chain_launch_shapes(api, tuning):
     ref = case.oracle_point(0)
     assert rel(out["chi2"][0].item(), ref["chi2"]) < 1e-6
     assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < 1e-6
+
+
+def test_repeated_evaluations_are_bit_identical(api):
+    # segment partials are summed in slot order and the point sums in bin
+    # order, whatever order the warps finish in
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, "ff", "split")
+    plan.tuning = "block=64 nodes=4"
+    p = plan.params_tensor(w.theta)
+    d = dev(case.data)
+    outs = [{k: v.clone() for k, v in plan.eval(p, d, grad=True, mu=True, spectra=True).items()} for _ in range(6)]
+    for o in outs[1:]:
+        for k in o:
+            assert torch.equal(o[k], outs[0][k]), k
+    plan.close()
 
 
 def test_chain_degenerate_shapes(api):

@@ -151,20 +151,24 @@ __global__ void k_build_grid(int nbins, int nbins_pad, const double* __restrict_
 }
 
 // Sum of the FP32 node weights of each bin, in double (for the epilogue's
-// exact correction of the constant term).
+// exact correction of the constant term): one warp per bin, lane l takes
+// nodes l, l + 32, ... (coalesced in layout 0), then a fixed-order butterfly.
 __global__ void k_sum_weights(const float4* __restrict__ grid, int nbins, int n, int layout, double* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= nbins) return;
     double s = 0.0;
-    for (int k = 0; k < n; k++) {
+    for (int k = lane; k < n; k += 32) {
         const int64_t pos = (layout == 0) ? (int64_t)i * n + k : (((int64_t)(i >> 5) * n + k) * 32 + (i & 31));
         s += (double)grid[pos].z;
     }
-    out[i] = s;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
 }
 
 cudaError_t launch_sum_weights(const float4* grid, int nbins, int n, int layout, double* out, cudaStream_t s) {
-    k_sum_weights<<<(nbins + 127) / 128, 128, 0, s>>>(grid, nbins, n, layout, out);
+    k_sum_weights<<<(unsigned)(((int64_t)nbins * 32 + 255) / 256), 256, 0, s>>>(grid, nbins, n, layout, out);
     return cudaGetLastError();
 }
 

@@ -159,7 +159,6 @@ struct gna_plan {
     double wsum_all_lo = 0.0;  // sum_r (om_r + omlo_r) - wsum: constant term when the weights enter as hi + lo
     // graphs are captured on a plan-owned stream joined to the caller's by events
     cudaStream_t cap_stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -455,8 +454,6 @@ gna_status gna_plan_destroy(gna_plan* plan) {
     if (plan->h_in) cudaFreeHost(plan->h_in);
     if (plan->h_out) cudaFreeHost(plan->h_out);
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
-    if (plan->ev_in) cudaEventDestroy(plan->ev_in);
-    if (plan->ev_out) cudaEventDestroy(plan->ev_out);
     for (void* v : plan->allocs) cudaFree(v);
     delete plan;
     return GNA_OK;
@@ -615,8 +612,6 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         }
     }
     CU(cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&plan->ev_in, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&plan->ev_out, cudaEventDisableTiming));
     // task list (bins mapping): (point, group) ordered by decreasing node count
     if (plan->has_bins) {
         if ((int64_t)d->npts * ngroups >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many bin groups");
@@ -762,12 +757,8 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
         plan->gkey = key;
         plan->graph_launches = nl;
     }
-    // join the caller's stream: caller -> plan stream -> graph -> caller
-    CU(cudaEventRecord(plan->ev_in, s));
-    CU(cudaStreamWaitEvent(cs, plan->ev_in, 0));
-    CU(cudaGraphLaunch(plan->gexec, cs));
-    CU(cudaEventRecord(plan->ev_out, cs));
-    CU(cudaStreamWaitEvent(s, plan->ev_out, 0));
+    // captured on the plan's own stream, replayed on the caller's
+    CU(cudaGraphLaunch(plan->gexec, s));
     plan->last_launches = plan->graph_launches;
     return GNA_OK;
 }
@@ -837,11 +828,7 @@ gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const doub
             plan->hkey = key;
             plan->graph_launches = nl;
         }
-        CU(cudaEventRecord(plan->ev_in, s));
-        CU(cudaStreamWaitEvent(cs, plan->ev_in, 0));
-        CU(cudaGraphLaunch(plan->hexec, cs));
-        CU(cudaEventRecord(plan->ev_out, cs));
-        CU(cudaStreamWaitEvent(s, plan->ev_out, 0));
+        CU(cudaGraphLaunch(plan->hexec, s));
         plan->last_launches = plan->graph_launches;
     } else {
         TRY(enqueue_all(s, &plan->last_launches));
@@ -921,15 +908,11 @@ gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, in
             cudaGetLastError();
             return fail(plan, GNA_ECUDA, "fit graph instantiate: %s", cudaGetErrorString(e));
         }
-        CU(cudaEventRecord(plan->ev_in, s));
-        CU(cudaStreamWaitEvent(cs, plan->ev_in, 0));
-        for (int it = 0; it < iters && e == cudaSuccess; it++) e = cudaGraphLaunch(ex, cs);
-        cudaError_t e2 = cudaEventRecord(plan->ev_out, cs);
-        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, plan->ev_out, 0);
+        for (int it = 0; it < iters && e == cudaSuccess; it++) e = cudaGraphLaunch(ex, s);
         cudaGraphExecDestroy(ex);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(plan, GNA_ECUDA, "fit graph launch: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+            return fail(plan, GNA_ECUDA, "fit graph launch: %s", cudaGetErrorString(e));
         }
         launches += iters * (nl + 1);
     } else {

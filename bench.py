@@ -56,13 +56,19 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     return nL * per_r + per_node
 
 
-# DRAM traffic of one launch of the benchmarked kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
-# sources it was taken with: reported as null once they change.
-TRAFFIC_CAPTURE = {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
-                   "bytes": 265113600 + 4114176}
+# DRAM traffic of one launch of the benchmarked kernels from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), per mapping, valid only for
+# the kernel sources it was taken with: reported as null once they change.
+TRAFFIC_CAPTURE = {
+    "split": {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
+              "bytes": 265113600 + 4114176},
+    "slices": {"sources_sha256": None, "bytes": None},
+}
 KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
-                  "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h"]
+                  "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h",
+                  "paper_1804_07682_gb300/csrc/slices.cu"]
+KERNEL_NAMES = {"split": "k_fused_split", "slices": "k_fused_bins (slices) + k_slices_reduce",
+                "bins": "k_fused_bins"}
 
 
 def kernel_sources_sha256() -> str:
@@ -459,10 +465,12 @@ def main():
     peak_tops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     pk, pk_src = peaks()
     hbm_bytes = 16 * w.nbins * w.nodes_per_bin
-    traffic = TRAFFIC_CAPTURE["bytes"] if TRAFFIC_CAPTURE["sources_sha256"] == kernel_sources_sha256() else None
+    mapping = plan.tuning.split()[0].split("=")[1]
+    cap = TRAFFIC_CAPTURE.get(mapping, {})
+    traffic = cap.get("bytes") if cap.get("sources_sha256") == kernel_sources_sha256() else None
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
                 "frac": achieved_tops / peak_tops, "traffic": traffic, "algorithmic_bytes": hbm_bytes,
-                "kernel": "k_fused_split (double-float phase, 8 baselines, gradient + spectra)",
+                "kernel": KERNEL_NAMES.get(mapping, mapping) + " (double-float phase, 8 baselines, gradient + spectra)",
                 "kernel_ms": kern_avg_ms, "ops_per_launch": ops,
                 "peak_note": "FP32 issue peak 152 SM x 128 lanes x 2070 MHz (FMA = 1 op)",
                 "hbm_frac": hbm_bytes / (kern_avg_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0),

@@ -87,8 +87,11 @@ typedef struct {
 } gna_plan_desc;
 
 #define GNA_PLAN_WITH_PLAIN 1  /* also build the FP64 arrays and scratch of gna_chain_eval_plain */
-#define GNA_PLAN_FORCE_SPLIT 2 /* CTA tiles split each bin's nodes (default for >= 1024 nodes/bin) */
+#define GNA_PLAN_FORCE_SPLIT 2 /* equal node ranges per warp across bins (default in FP64 for >= 1024 nodes/bin) */
 #define GNA_PLAN_FORCE_BINS 4  /* one thread per bin (default for small or per-point grids) */
+#define GNA_PLAN_FORCE_SLICES 8 /* one thread per bin and slice of its nodes, slices summed by a
+                                   second kernel (default for uniform grids in the mixed
+                                   precisions when points x bin groups are too few to fill the GPU) */
 
 /* Outputs of one evaluation (device pointers; any may be NULL except chi2). */
 typedef struct {

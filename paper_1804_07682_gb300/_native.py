@@ -20,6 +20,7 @@ GNA_PEARSON, GNA_POISSON = 0, 1
 GNA_PLAN_WITH_PLAIN = 1
 GNA_PLAN_FORCE_SPLIT = 2
 GNA_PLAN_FORCE_BINS = 4
+GNA_PLAN_FORCE_SLICES = 8
 
 
 class GnaOsc(ctypes.Structure):

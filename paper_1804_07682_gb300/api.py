@@ -89,6 +89,10 @@ class Plan:
             flags |= N.GNA_PLAN_FORCE_SPLIT
         elif mapping == "bins":
             flags |= N.GNA_PLAN_FORCE_BINS
+        elif mapping == "slices":
+            flags |= N.GNA_PLAN_FORCE_SLICES
+        elif mapping is not None:
+            raise ValueError("mapping must be 'split', 'bins', 'slices' or None")
         P = ctypes.POINTER(ctypes.c_double)
         d = N.GnaPlanDesc()
         d.nbins = self.nbins

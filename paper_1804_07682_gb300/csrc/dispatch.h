@@ -10,4 +10,8 @@ cudaError_t dispatch_split(int ph, int nl, bool grad, bool spec, const void* arg
 cudaError_t dispatch_bins(int ph, int nl, bool grad, bool spec, const void* args, int grid, int block, cudaStream_t s);
 // registers per thread of the split kernel (for occupancy-aware grid sizing)
 int split_regs(int ph, int nl, bool grad, bool spec);
+// second step of the slice mapping (slices.cu): S slices of NV values per
+// (point, group) in part [npts][ngroups][S][NV][32]
+struct EpiArgs;
+cudaError_t launch_slices_reduce(const float2* part, int S, int NV, const EpiArgs& ea, int npts, cudaStream_t s);
 }  // namespace gna

@@ -23,6 +23,9 @@
 
 namespace gna {
 
+// Largest number of values per (point, bin): chi2, four tangents, 16 spectra.
+constexpr int kMaxNV = 1 + 4 + GNA_NLMAX;
+
 struct EpiArgs {
     int is64;
     int NV, has_grad, nspec, nL_out;

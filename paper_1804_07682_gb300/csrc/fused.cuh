@@ -269,11 +269,18 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
 
 // ---------------------------------------------------------------------------
 // Bin mapping: a warp task is (point p, group b of 32 consecutive bins); lane
-// l owns bin 32 b + l and walks all its nodes (grid layout [group][k][lane],
-// so each warp load is 512 contiguous bytes, the next one prefetched).  Each
-// lane finishes its own bin; the last warp of a point reduces the point.
-// Warps take tasks from a global counter; tasks are ordered by decreasing
-// node count so that uneven grids balance.
+// l owns bin 32 b + l and walks its nodes (grid layout [group][k][lane], so
+// each warp load is 512 contiguous bytes, the next one prefetched).  Each
+// lane finishes its own bin; the warp sums its group and the last group of a
+// point sums the groups.  Warps take tasks from a global counter; tasks are
+// ordered by decreasing node count so that uneven grids balance.
+//
+// Slice mapping (S > 1, one grid shared by all points): the same kernel with
+// each group's nodes cut into S slices of L nodes; task t = (p, b, s) in
+// that order.  A lane keeps its own bin's sums for its slice and stores them
+// as float pairs; k_slices_reduce then sums the slices in order and runs the
+// epilogue.  Unlike the split mapping no warp reduction or counter is needed
+// per node range, and the node loop is the same as for whole bins.
 struct BinArgs {
     const float4* grid;
     const int64_t* goff;  // [ngrids] float4 offset of each grid
@@ -285,6 +292,8 @@ struct BinArgs {
     BaseConst bc;
     int* counter;  // zeroed before the launch
     EpiArgs ea;
+    int S, L;      // slices per group and nodes per slice (S = 1: whole bins)
+    float2* part;  // slice values [ntasks][NV][32] (S > 1)
 };
 
 template <int PH, int NL, bool GRAD, bool SPEC>
@@ -299,11 +308,23 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
         if (lane == 0) t = atomicAdd(a.counter, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= a.ntasks) break;
-        const int task = a.tasks[t];
-        const int p = task / a.ngroups;
-        const int b = task - p * a.ngroups;
+        int p, b, k0, n;
+        if (a.S > 1) {
+            const int per_point = a.ngroups * a.S;
+            p = t / per_point;
+            const int rem = t - p * per_point;
+            b = rem / a.S;
+            k0 = (rem - b * a.S) * a.L;
+            n = a.gn[0];
+        } else {
+            const int task = a.tasks[t];
+            p = task / a.ngroups;
+            b = task - p * a.ngroups;
+            k0 = 0;
+            n = a.gn[a.shared_grid ? 0 : p];
+        }
         const int gi = a.shared_grid ? 0 : p;
-        const int n = a.gn[gi];
+        const int kn = min(n, k0 + (a.S > 1 ? a.L : n)) - k0;  // nodes of this task per lane
         if (p != last_p) {
             m.load(a.pcs + p, a.bc);
             last_p = p;
@@ -311,26 +332,34 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
         KahanF acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) kzero(acc[v]);
-        const float4* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
+        const float4* g = a.grid + a.goff[gi] + ((int64_t)b * n + k0) * 32 + lane;
         // ring of D nodes in flight: with few baselines a node is too little
         // work to cover the load latency of the next one
         constexpr int D = (NL >= 4) ? 1 : 4;
         float4 buf[D];
 #pragma unroll
-        for (int j = 0; j < D; j++) buf[j] = (j < n) ? __ldg(g + (int64_t)j * 32) : make_float4(1.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < D; j++) buf[j] = (j < kn) ? __ldg(g + (int64_t)j * 32) : make_float4(1.f, 0.f, 0.f, 0.f);
         int k = 0;
-        for (; k + D <= n; k += D) {
+        for (; k + D <= kn; k += D) {
 #pragma unroll
             for (int j = 0; j < D; j++) {
                 const float4 cur = buf[j];
-                const int kn = k + j + D;
-                buf[j] = (kn < n) ? __ldg(g + (int64_t)kn * 32) : cur;
+                const int kx = k + j + D;
+                buf[j] = (kx < kn) ? __ldg(g + (int64_t)kx * 32) : cur;
                 m.update(cur, acc);
             }
         }
 #pragma unroll
         for (int j = 0; j < D; j++)
-            if (k + j < n) m.update(buf[j], acc);
+            if (k + j < kn) m.update(buf[j], acc);
+        if (a.S > 1) {
+            float2* pp = a.part + (int64_t)t * NV * 32 + lane;
+#pragma unroll
+            for (int v = 0; v < NV; v++) pp[v * 32] = kahan_to_ff(acc[v]);
+            // the slice reduction (a programmatic dependent launch) may start
+            // placing its blocks once this warp's last task is done
+            continue;
+        }
         const int i = b * 32 + lane;
         if (i < a.nbins) {
             double v[NV];
@@ -340,6 +369,7 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
         }
         group_done(a.ea, p, b, lane);
     }
+    asm volatile("griddepcontrol.launch_dependents;");
 }
 
 template <int PH, int NL, bool GRAD, bool SPEC>

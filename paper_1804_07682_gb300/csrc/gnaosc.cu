@@ -53,7 +53,7 @@ int split_regs(int ph, int nl, bool grad, bool spec) {
 
 namespace {
 
-enum { MAP_SPLIT = 0, MAP_BINS = 1 };
+enum { MAP_SPLIT = 0, MAP_BINS = 1, MAP_SLICES = 2 };
 const int kDefaultBlock = 256;
 const int kDefaultNodesPerThread = 16;
 
@@ -108,6 +108,8 @@ struct gna_plan {
     int* d_counters = nullptr;
     int64_t ncounters = 0;
     int maxseg_cap = 2;  // split mapping: partial slots per (point, bin) the plan allocated
+    int slices_cap = 0;  // slice mapping: slices per group the plan allocated (0: unavailable)
+    float2* d_slices = nullptr;  // [npts][ngroups][slices][NV][32]
     double* d_edges = nullptr;
     // constants
     BaseConst bc{};
@@ -129,6 +131,7 @@ struct gna_plan {
     LMState* d_lm = nullptr;
     // launch shape
     int block = kDefaultBlock, npt = kDefaultNodesPerThread, grid_mult = 0;
+    int slice_len = 0;  // slice mapping: nodes per slice (0: chosen from the GPU size)
     // graphs
     bool use_graph = false;
     cudaGraphExec_t gexec = nullptr;
@@ -237,7 +240,6 @@ SplitShape split_shape(const gna_plan* p, bool grad, bool spec) {
     return sh;
 }
 
-int nchunks_of(const gna_plan* p) { return 1; }
 
 int value_count(const gna_plan* p, bool grad, bool spec) { return fused_nv(p->nl_inst, grad, spec); }
 
@@ -259,6 +261,32 @@ int grid_size(const gna_plan* p, bool grad, bool spec, int64_t work_items) {
     int64_t g = (int64_t)p->sm_count * resident_ctas_per_sm(p, grad, spec);
     g = std::min<int64_t>(g, (work_items * 32 + p->block - 1) / p->block);
     return (int)std::max<int64_t>(1, g);
+}
+
+// Slice mapping: S slices of L nodes per group of 32 bins.  The default L
+// gives about two tasks per resident warp (estimate: 16 warps per SM), so
+// that the task counter can even out the warps the schedulers favour.
+struct SliceShape {
+    int S, L, ntasks;
+};
+
+SliceShape slice_shape(const gna_plan* p) {
+    const int n = p->n_uniform;
+    const int64_t pg = (int64_t)p->npts * p->ngroups;
+    int64_t L = p->slice_len;
+    if (L <= 0) {
+        const int64_t target = 2LL * 16 * p->sm_count;
+        const int64_t S = std::max<int64_t>(1, (target + pg - 1) / pg);
+        L = (n + S - 1) / S;
+    }
+    if (p->slices_cap <= 1) L = n;
+    else L = std::max<int64_t>(L, (n + p->slices_cap - 1) / p->slices_cap);
+    L = std::min<int64_t>(std::max<int64_t>(L, 1), n);
+    SliceShape sh;
+    sh.L = (int)L;
+    sh.S = (int)((n + L - 1) / L);
+    sh.ntasks = (int)(pg * sh.S);
+    return sh;
 }
 
 struct EvalReq {
@@ -287,6 +315,11 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
         if ((size_t)plan->npts * plan->nbins * sh.maxseg * NV > plan->part_cap)
             return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
                         (long long)plan->npts * plan->nbins * sh.maxseg * NV, plan->part_cap);
+    }
+    SliceShape ssh{1, 0, plan->ntasks};
+    if (plan->mapping == MAP_SLICES) {
+        ssh = slice_shape(plan);
+        if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
     }
     // work counter, per-point and per-bin arrival counters: one memset
     const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups) +
@@ -343,11 +376,22 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
                           plan->d_pc, plan->bc, (double*)plan->d_part, ea};
             CU(dispatch_split(2, plan->nl_inst, grad, spec, &a, sh.grid, plan->block, s));
         }
+    } else if (plan->mapping == MAP_SLICES) {
+        const int g = grid_size(plan, grad, spec, ssh.ntasks);
+        const bool sliced = ssh.S > 1;
+        BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, ssh.ntasks,
+                  plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea,
+                  ssh.S, ssh.L, sliced ? plan->d_slices : nullptr};
+        CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
+        if (sliced) {
+            CU(launch_slices_reduce(plan->d_slices, ssh.S, NV, ea, plan->npts, s));
+            nl++;
+        }
     } else {
         const int g = grid_size(plan, grad, spec, plan->ntasks);
         if (plan->ph < 2) {
             BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
-                      plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea};
+                      plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, 1, 0, nullptr};
             CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         } else {
             BinArgs64 a{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
@@ -522,18 +566,30 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     // mapping and layouts
     const int ngroups = (d->nbins + 31) / 32;
     plan->ngroups = ngroups;
-    if ((d->flags & GNA_PLAN_FORCE_SPLIT) && !plan->uniform)
-        return fail(plan, GNA_EINVAL, "the split mapping needs equal node counts for all points");
+    if ((d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_SLICES)) && !plan->uniform)
+        return fail(plan, GNA_EINVAL, "the split and slice mappings need equal node counts for all points");
+    if ((d->flags & GNA_PLAN_FORCE_SLICES) && plan->ph == 2)
+        return fail(plan, GNA_EINVAL, "the slice mapping is for the mixed precisions");
+    // slices of a group's nodes give enough warp tasks when the points x
+    // groups alone do not (estimate: 16 resident warps per SM)
+    const int64_t warps_est = 16LL * plan->sm_count;
+    const bool slices_ok = plan->uniform && plan->ph < 2;
     if (d->flags & GNA_PLAN_FORCE_SPLIT) plan->mapping = MAP_SPLIT;
     else if (d->flags & GNA_PLAN_FORCE_BINS) plan->mapping = MAP_BINS;
+    else if (d->flags & GNA_PLAN_FORCE_SLICES) plan->mapping = MAP_SLICES;
+    else if (slices_ok && (int64_t)d->npts * ngroups < 4 * warps_est) plan->mapping = MAP_SLICES;
     else if (plan->uniform && (plan->n_uniform >= 1024 || (int64_t)d->npts * ngroups < 16LL * plan->sm_count))
         plan->mapping = MAP_SPLIT;
     else plan->mapping = MAP_BINS;
-    const bool forced = (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_BINS)) != 0;
+    const bool forced = (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_BINS | GNA_PLAN_FORCE_SLICES)) != 0;
     const bool small = plan->uniform && (int64_t)d->nbins * plan->n_uniform <= (1LL << 20) &&
                        (int64_t)d->npts * d->nbins <= (1LL << 16);
-    plan->has_split = plan->mapping == MAP_SPLIT || (!forced && small);
-    plan->has_bins = plan->mapping == MAP_BINS || (!forced && small);
+    // a default slice mapping keeps the split layout too (grids up to 2^26
+    // nodes), so that the autotuner can compare the two
+    const bool keep_split = plan->mapping == MAP_SLICES && !forced &&
+                            (int64_t)d->nbins * plan->n_uniform <= (1LL << 26);
+    plan->has_split = plan->mapping == MAP_SPLIT || (!forced && small) || keep_split;
+    plan->has_bins = plan->mapping == MAP_BINS || plan->mapping == MAP_SLICES || (!forced && small);
     const bool shared = plan->uniform;
     plan->ngrids = shared ? 1 : d->npts;
     const int nbins_pad = ngroups * 32;
@@ -640,6 +696,15 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         plan->maxseg_cap = (int)std::min(by_len, by_mem);
         plan->part_cap = (size_t)pairs * plan->maxseg_cap * nv_max;
         TRY(dalloc(plan, (double**)&plan->d_part, plan->part_cap));
+    }
+    if (slices_ok && plan->has_bins) {
+        // slices per group: up to 8 tasks per resident warp, at least 16 nodes per slice
+        const int64_t pg = (int64_t)d->npts * ngroups;
+        const int64_t by_tasks = (8 * warps_est + pg - 1) / pg;
+        const int64_t by_len = std::max<int64_t>(1, plan->n_uniform / 16);
+        plan->slices_cap = (int)std::max<int64_t>(1, std::min(by_tasks, by_len));
+        if (plan->slices_cap > 1)
+            TRY(dalloc(plan, &plan->d_slices, (size_t)pg * plan->slices_cap * nv_max * 32));
     }
     TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
     TRY(dalloc(plan, &plan->d_gvals, (size_t)d->npts * ngroups * 15));
@@ -930,35 +995,42 @@ gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, in
 
 gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen) {
     if (!plan || !buf || buflen < 1) return GNA_EINVAL;
-    snprintf(buf, buflen, "mapping=%s block=%d nodes=%d grid=%d", plan->mapping == MAP_SPLIT ? "split" : "bins",
-             plan->block, plan->npt, plan->grid_mult);
+    static const char* names[3] = {"split", "bins", "slices"};
+    snprintf(buf, buflen, "mapping=%s block=%d nodes=%d grid=%d slice=%d", names[plan->mapping], plan->block, plan->npt,
+             plan->grid_mult, plan->slice_len);
     return GNA_OK;
 }
 
 gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     if (!plan || !text) return GNA_EINVAL;
-    int block = plan->block, npt = plan->npt, gm = plan->grid_mult, mapping = plan->mapping;
+    int block = plan->block, npt = plan->npt, gm = plan->grid_mult, mapping = plan->mapping, sl = plan->slice_len;
     const char* b = strstr(text, "block=");
     const char* n = strstr(text, "nodes=");
     const char* g = strstr(text, "grid=");
     const char* m = strstr(text, "mapping=");
+    const char* c = strstr(text, "slice=");
     if (b) block = atoi(b + 6);
     if (n) npt = atoi(n + 6);
     if (g) gm = atoi(g + 5);
+    if (c) sl = atoi(c + 6);
     if (m) {
         if (!strncmp(m + 8, "split", 5)) mapping = MAP_SPLIT;
         else if (!strncmp(m + 8, "bins", 4)) mapping = MAP_BINS;
+        else if (!strncmp(m + 8, "slices", 6)) mapping = MAP_SLICES;
         else return fail(plan, GNA_EINVAL, "bad mapping in '%s'", text);
     }
-    if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64)
+    if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64 || sl < 0)
         return fail(plan, GNA_EINVAL, "bad tuning '%s'", text);
-    if ((mapping == MAP_SPLIT && !plan->has_split) || (mapping == MAP_BINS && !plan->has_bins))
-        return fail(plan, GNA_EINVAL, "the plan has no grid for the %s mapping", mapping == MAP_SPLIT ? "split" : "bins");
+    if ((mapping == MAP_SPLIT && !plan->has_split) || (mapping == MAP_BINS && !plan->has_bins) ||
+        (mapping == MAP_SLICES && (!plan->has_bins || !plan->uniform || plan->ph == 2)))
+        return fail(plan, GNA_EINVAL, "the plan has no grid for the %s mapping",
+                    mapping == MAP_SPLIT ? "split" : mapping == MAP_BINS ? "bins" : "slices");
     if (mapping == MAP_SPLIT && npt < 4) return fail(plan, GNA_EINVAL, "nodes per lane must be >= 4");
     plan->block = block;
     plan->npt = npt;
     plan->grid_mult = gm;
     plan->mapping = mapping;
+    plan->slice_len = sl;
     destroy_graph(plan);
     return GNA_OK;
 }
@@ -988,6 +1060,17 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
             snprintf(t, sizeof(t), "mapping=bins block=%d nodes=1", b);
             cand.push_back(t);
         }
+    if (plan->has_bins && plan->uniform && plan->ph < 2 && plan->slices_cap > 1) {
+        // slice lengths for about 1, 2 and 4 tasks per resident warp
+        const int64_t pg = (int64_t)plan->npts * plan->ngroups;
+        for (int b : {128, 256})
+            for (int tpw : {1, 2, 4}) {
+                const int64_t S = std::max<int64_t>(1, ((int64_t)tpw * 16 * plan->sm_count + pg - 1) / pg);
+                const int64_t L = (plan->n_uniform + S - 1) / S;
+                snprintf(t, sizeof(t), "mapping=slices block=%d slice=%lld", b, (long long)L);
+                cand.push_back(t);
+            }
+    }
     char best_t[128];
     gna_plan_get_tuning(plan, best_t, sizeof(best_t));
     float best = 1e30f;

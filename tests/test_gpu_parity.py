@@ -129,10 +129,28 @@ def test_chain_small(api, name, prec):
     check_chain(api, get_case(name), prec)
 
 
-@pytest.mark.parametrize("mapping", ["split", "bins"])
+@pytest.mark.parametrize("mapping", ["split", "bins", "slices"])
 @pytest.mark.parametrize("name", ["reactor_200x50", "reactor8_40x3000", "fits_8x100x20"])
-def test_chain_both_mappings(api, name, mapping):
+def test_chain_all_mappings(api, name, mapping):
     check_chain(api, get_case(name), "ff", mapping)
+
+
+@pytest.mark.parametrize("prec", ["f64phase", "ff"])
+@pytest.mark.parametrize("tuning", ["slice=16", "slice=7", "slice=100 block=64", "slice=3000 block=128", "slice=999"])
+def test_slice_shapes(api, prec, tuning):
+    # slices of 7 ... 3000 nodes of 3000-node bins (ragged last slice), spectra on
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, prec, "slices")
+    plan.tuning = tuning
+    out = plan.eval(plan.params_tensor(w.theta), dev(case.data), grad=True, mu=True, spectra=True)
+    ref = case.oracle_point(0)
+    tol = TOL[prec]
+    assert abs(out["chi2"][0].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, case.data, w.kind)
+    assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < tol
+    assert rel(out["spectra"][0].cpu().numpy(), ref["mu_rb"]) < tol
+    assert normrel(out["grad"][0].cpu().numpy(), ref["grad"][:4]) < GTOL[prec]
+    plan.close()
 
 
 @pytest.mark.parametrize("tuning", ["block=64 nodes=4", "block=128 nodes=7", "block=256 nodes=64", "block=96 nodes=5",
@@ -148,13 +166,14 @@ def test_chain_launch_shapes(api, tuning):
     assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < 1e-6
 
 
-def test_repeated_evaluations_are_bit_identical(api):
-    # segment partials are summed in slot order and the point sums in bin
-    # order, whatever order the warps finish in
+@pytest.mark.parametrize("mapping,tuning", [("split", "block=64 nodes=4"), ("slices", "block=64 slice=20")])
+def test_repeated_evaluations_are_bit_identical(api, mapping, tuning):
+    # segment and slice values are summed in slot order and the point sums in
+    # bin order, whatever order the warps finish in
     case = get_case("reactor8_40x3000")
     w = case.w
-    plan = make_plan(api, case, "ff", "split")
-    plan.tuning = "block=64 nodes=4"
+    plan = make_plan(api, case, "ff", mapping)
+    plan.tuning = tuning
     p = plan.params_tensor(w.theta)
     d = dev(case.data)
     outs = [{k: v.clone() for k, v in plan.eval(p, d, grad=True, mu=True, spectra=True).items()} for _ in range(6)]
@@ -177,8 +196,8 @@ def test_chain_degenerate_shapes(api):
         check_chain(api, case2, prec)
 
 
-@pytest.mark.parametrize("mapping", ["split", "bins"])
-@pytest.mark.parametrize("nbins,n,npts", [(1, 8, 40), (3, 5, 50), (2, 16, 3), (7, 3, 33)])
+@pytest.mark.parametrize("mapping", ["split", "bins", "slices"])
+@pytest.mark.parametrize("nbins,n,npts", [(1, 8, 40), (3, 5, 50), (2, 16, 3), (7, 3, 33), (2, 40, 3)])
 def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):
     # the whole grid (bins x nodes) has fewer nodes than a warp has lanes, so a
     # lane's next node lies several bins, or several points, further on
@@ -186,7 +205,7 @@ def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):
     theta = np.tile(np.array(wl.TRUTH), (npts, 1)) * rng.uniform(0.9, 1.1, size=(npts, 4))
     w = wl.Workload("tiny", np.linspace(2.0, 8.0, nbins + 1), n, np.array([52.5, 53.0]), theta, wl.POISSON)
     case = Case(w)
-    for prec in ("fp64", "ff"):
+    for prec in (("f64phase", "ff") if mapping == "slices" else ("fp64", "ff")):
         check_chain(api, case, prec, mapping)
 
 
@@ -247,7 +266,11 @@ def test_mapping_is_a_tuning_choice_on_small_grids(api, prec):
     ref = case.oracle_point(0)
     tol = TOL[prec]
     res = {}
-    for m in ("split", "bins"):
+    from paper_1804_07682_gb300 import _native as N
+    if prec == "fp64":
+        with pytest.raises(N.GnaError):
+            plan.tuning = "mapping=slices"
+    for m in ("split", "bins") + (("slices",) if prec != "fp64" else ()):
         plan.tuning = f"mapping={m} block=128 nodes=4"
         assert plan.tuning.startswith(f"mapping={m}")
         out = plan.eval(p, d, grad=True, mu=True)

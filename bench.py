@@ -420,7 +420,7 @@ def main():
     if args.tuning:
         plan.tuning = args.tuning
     elif not args.no_autotune:
-        plan.autotune(params, data, reps=5)
+        plan.autotune(params, data, reps=20, grad=True, spectra=True)
     out = {"chi2": torch.empty(1, dtype=torch.float64, device=device),
            "grad": torch.empty(1, 4, dtype=torch.float64, device=device),
            "spectra": torch.empty(1, w.nL, w.nbins, dtype=torch.float64, device=device)}

@@ -217,14 +217,17 @@ gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, in
 
 /* ---------------------------------------------------------------------------
  * Launch shape, autotuning and graphs.
- * gna_plan_autotune: times the candidate launch shapes (threads per block,
- * nodes per thread, grid size) for this plan on `stream` with CUDA events
- * over `reps` evaluations each (with the given arguments, gradient on) and
- * keeps the fastest.  The choice can be read back and restored as text
- * ("block=256 nodes=16 grid=1216") for caching between runs.
+ * gna_plan_autotune: times the candidate mappings and launch shapes (node
+ * mapping, threads per block, nodes per lane, slice length) for this plan on
+ * `stream` with CUDA events over `reps` evaluations each and keeps the
+ * fastest.  The evaluations write the outputs `out` names (device pointers,
+ * as for gna_chain_eval: the kernels differ with the outputs requested), or,
+ * with out == NULL, chi^2 and the gradient into plan scratch.  The choice can
+ * be read back and restored as text ("mapping=slices block=256 nodes=16
+ * grid=0 slice=216") for caching between runs.
  */
 gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point,
-                             int reps, void* stream);
+                             const gna_outputs* out, int reps, void* stream);
 gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen);
 gna_status gna_plan_set_tuning(gna_plan* plan, const char* text);
 

@@ -234,9 +234,20 @@ class Plan:
         self._check(code, "gna_fit_batch")
         return params, chi2_out
 
-    def autotune(self, params: torch.Tensor, data: torch.Tensor, reps: int = 3, stream=None) -> str:
+    def autotune(self, params: torch.Tensor, data: torch.Tensor, reps: int = 3, grad: bool = True,
+                 mu: bool = False, spectra: bool = False, stream=None) -> str:
+        """Times the candidate mappings and launch shapes with the outputs the
+        caller will ask for (the kernels differ with them) and keeps the fastest."""
         dpp = 1 if data.dim() == 2 else 0
-        code = self._lib.gna_plan_autotune(self._h, _ptr(params), _ptr(data), dpp, int(reps),
+        out = {"chi2": self._out("chi2", (self.npts,))}
+        if grad:
+            out["grad"] = self._out("grad", (self.npts, 4))
+        if mu:
+            out["mu"] = self._out("mu", (self.npts, self.nbins))
+        if spectra:
+            out["spectra"] = self._out("spectra", (self.npts, self.nL, self.nbins))
+        o = N.GnaOutputs(_ptr(out["chi2"]), _ptr(out.get("grad")), None, _ptr(out.get("mu")), _ptr(out.get("spectra")))
+        code = self._lib.gna_plan_autotune(self._h, _ptr(params), _ptr(data), dpp, ctypes.byref(o), int(reps),
                                            ctypes.c_void_p(_stream(stream)))
         self._check(code, "gna_plan_autotune")
         return self.tuning

@@ -10,11 +10,12 @@
 // The last bin of a point to finish sums the per-bin values over bins in a
 // fixed order (deterministic) and writes chi2, the gradient and J^T W J.
 //
-// In the mixed modes only mu_i and t_i = (d_i - mu_i) / mu_i are formed in
-// double (FP64 instructions are 1/64 of the FP32 rate on this part); the
-// Poisson term 2 mu_i h(t_i), h(t) = (1 + t) log1p(t) - t, the adjoint g_i and
-// the gradient and J^T W J terms are FP32 (their relative error, ~1e-7, is
-// far inside the mixed-mode tolerance).  Per-bin values are stored as float
+// In the mixed modes only mu_i and d_i - mu_i are formed in double (FP64
+// instructions are 1/64 of the FP32 rate on this part); t_i = (d_i - mu_i) /
+// mu_i, the Poisson term 2 mu_i h(t_i), h(t) = (1 + t) log1p(t) - t, the
+// adjoint g_i, the gradient and J^T W J terms and the corrections of the FP32
+// weights are FP32 (relative error ~1e-7 in each bin's term, far inside the
+// mixed-mode tolerance).  Per-bin values are stored as float
 // pairs (hi + lo) and summed over bins in double-float arithmetic.
 #pragma once
 
@@ -43,8 +44,8 @@ struct EpiArgs {
     int NBV;               // 1 (chi2), 5 (+ gradient), 15 (+ J^T W J)
     const double* sumW;    // [ngrids][nbins] summed FP32 node weights (mixed modes)
     int shared_grid;
-    double wsum_lo;
-    double om_delta[GNA_NLMAX];  // omega_r - om_r
+    float wsum_lo;               // exact sum of the FP32 weights - the kernel's constant term
+    float om_delta[GNA_NLMAX];   // omega_r - om_r (corrections ~1e-8 relative: FP32 suffices)
     double* chi2;          // [npts]
     double* grad;          // [npts][4] or NULL
     double* H;             // [npts][10] or NULL
@@ -73,8 +74,28 @@ __device__ __forceinline__ float poisson_h(float t) {
     return fmaf(1.0f + t, log1pf(t), -t);
 }
 
-// v: the NV summed values of (p, i): [0] sum W Pc, [1..4] tangent sums, [off + r] per-baseline sums.
-__device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double* v) {
+// Inputs of one bin's epilogue that do not depend on the node sums (so that
+// a caller may load them before the sums are ready).
+struct BinIn {
+    double d;     // data count
+    double e;     // nuisance eta_i (0 without nuisances)
+    double sumw;  // summed FP32 node weights (mixed modes; 0 without)
+};
+
+__device__ __forceinline__ BinIn bin_inputs(const EpiArgs& a, int p, int i) {
+    const int64_t idx = (int64_t)p * a.nbins + i;
+    BinIn in;
+    in.d = a.data[a.data_per_point ? idx : i];
+    in.e = a.eta ? a.eta[i] : 0.0;
+    in.sumw = a.sumW ? a.sumW[(a.shared_grid ? 0 : (int64_t)p * a.nbins) + i] : 0.0;
+    return in;
+}
+
+// v: the NV summed values of (p, i): [0] sum W Pc, [1..4] tangent sums, [off + r]
+// per-baseline sums.  The NBV per-bin values go to binvals, or, with regs, to
+// the caller's registers (when the caller's warp reduces its own group).
+__device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double* v, const BinIn& in,
+                                    float2* regs = nullptr) {
     const int64_t idx = (int64_t)p * a.nbins + i;
     double M = v[0];
     const int off = 1 + (a.has_grad ? 4 : 0);
@@ -82,14 +103,15 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
         // exact corrections of the FP32 weights: the constant term of P carries
         // wsum_lo times the bin's summed node weights, and with per-baseline
         // sums the rounding of omega_r is undone with those sums
-        if (a.sumW) M += a.wsum_lo * a.sumW[(a.shared_grid ? 0 : (int64_t)p * a.nbins) + i];
+        float corr = a.wsum_lo * (float)in.sumw;
         if (a.nspec > 0)
-            for (int r = 0; r < a.nL_out; r++) M += a.om_delta[r] * v[off + r];
+            for (int r = 0; r < a.nL_out; r++) corr = fmaf(a.om_delta[r], (float)v[off + r], corr);
+        M += (double)corr;
     }
-    const double e = a.eta ? a.eta[i] : 0.0;
+    const double e = in.e;
     const double f = a.norm * (1.0 + e);
     const double mu = f * M;
-    const double d = a.data[a.data_per_point ? idx : i];
+    const double d = in.d;
     double term;
     float g;
     if (a.is64) {
@@ -102,7 +124,7 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
             gd = 2.0 * (1.0 - d / mu);
         }
         g = (float)gd;
-        float2* bv = a.binvals + idx * a.NBV;
+        float2* bv = regs ? regs : a.binvals + idx * a.NBV;
         const bool pen = a.eta && a.sigma > 0.0;
         if (pen) term += e * e / (a.sigma * a.sigma);
         bv[0] = to_ff(term);
@@ -122,17 +144,16 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
         if (a.mu_out) a.mu_out[idx] = mu;
         if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
     } else {
-        const double dm = d - mu;
-        const double t = dm / mu;  // the one FP64 division
+        const double dm = d - mu;                   // in double: d and mu are close
+        const float tf = (float)dm / (float)mu;     // relative residual, 1e-7 is enough
         if (a.kind == GNA_PEARSON) {
-            term = dm * t;  // (d - mu)^2 / mu
-            const float tf = (float)t;
+            term = dm * (double)tf;  // (d - mu)^2 / mu
             g = 1.0f - (1.0f + tf) * (1.0f + tf);  // 1 - d^2 / mu^2
         } else {
-            term = (d > 0.0) ? 2.0 * mu * (double)poisson_h((float)t) : 2.0 * mu;
-            g = -2.0f * (float)t;  // 2 (1 - d / mu)
+            term = (d > 0.0) ? 2.0 * mu * (double)poisson_h(tf) : 2.0 * mu;
+            g = -2.0f * tf;  // 2 (1 - d / mu)
         }
-        float2* bv = a.binvals + idx * a.NBV;
+        float2* bv = regs ? regs : a.binvals + idx * a.NBV;
         const bool pen = a.eta && a.sigma > 0.0;
         if (pen) term += e * e / (a.sigma * a.sigma);
         bv[0] = to_ff(term);
@@ -166,14 +187,19 @@ __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double
 // two short reductions after the last bin instead of one over all bins.
 // Reads go through L2 (__ldcg): other SMs wrote the values.
 
-// Group g of point p: lane l takes bin 32 g + l; lanes of the group whose
-// sum is stored hold value lane / 2 after the transposed reduction.
-__device__ inline void group_reduce(const EpiArgs& a, int p, int g, int lane) {
+// Group g of point p: lane l holds (regs) or loads (binvals) the values of
+// bin 32 g + l; one transposed reduction; lanes holding value lane / 2 store it.
+__device__ inline void group_reduce(const EpiArgs& a, int p, int g, int lane, const float2* regs) {
     const int i = (g << 5) + lane;
-    const float2* bv = a.binvals + ((int64_t)p * a.nbins + i) * a.NBV;
     float2 v[16];
+    if (regs) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) v[j] = (j < a.NBV && i < a.nbins) ? __ldcg(bv + j) : make_float2(0.f, 0.f);
+        for (int j = 0; j < 16; j++) v[j] = (j < a.NBV && i < a.nbins) ? regs[j] : make_float2(0.f, 0.f);
+    } else {
+        const float2* bv = a.binvals + ((int64_t)p * a.nbins + i) * a.NBV;
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = (j < a.NBV && i < a.nbins) ? __ldcg(bv + j) : make_float2(0.f, 0.f);
+    }
     warp_transpose_reduce<16>(v, lane);
     const int vi = lane >> 1;
     if ((lane & 1) == 0 && vi < a.NBV) a.gvals[((int64_t)p * a.ngroups + g) * a.NBV + vi] = v[0];
@@ -204,17 +230,20 @@ __device__ inline void point_reduce(const EpiArgs& a, int p, int lane) {
     }
 }
 
-// The whole group g of point p has its per-bin values stored (whole warp
-// calls).  Not inlined: its registers stay out of the node loops' allocation.
-static __device__ __noinline__ void group_done(const EpiArgs& a, int p, int g, int lane) {
+// The whole group g of point p has its per-bin values ready (whole warp
+// calls): in regs (each lane its bin's values) or in binvals.  Not inlined:
+// its registers stay out of the node loops' allocation.
+static __device__ __noinline__ void group_done(const EpiArgs& a, int p, int g, int lane, const float2* regs) {
+    if (!regs) {
+        __threadfence();
+        __syncwarp();
+    }
+    group_reduce(a, p, g, lane, regs);
+    // every lane that stored a group value makes it visible before lane 0 counts the group
     __threadfence();
     __syncwarp();
-    group_reduce(a, p, g, lane);
     int lastp = 0;
-    if (lane == 0) {
-        __threadfence();
-        lastp = (atomicAdd(a.pt_cnt + p, 1) == a.ngroups - 1);
-    }
+    if (lane == 0) lastp = (atomicAdd(a.pt_cnt + p, 1) == a.ngroups - 1);
     lastp = __shfl_sync(0xffffffffu, lastp, 0);
     if (lastp) {
         __threadfence();
@@ -232,7 +261,7 @@ __device__ inline void bin_done(const EpiArgs& a, int p, int i, int lane) {
         lastg = (atomicAdd(a.grp_cnt + (int64_t)p * a.ngroups + g, 1) == gsize - 1);
     }
     lastg = __shfl_sync(0xffffffffu, lastg, 0);
-    if (lastg) group_done(a, p, g, lane);
+    if (lastg) group_done(a, p, g, lane, nullptr);
 }
 
 }  // namespace gna

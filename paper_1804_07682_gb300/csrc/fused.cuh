@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
             double sv[NV];
 #pragma unroll
             for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
-            if (lane == 0) bin_epilogue(a.ea, p, i, sv);
+            if (lane == 0) bin_epilogue(a.ea, p, i, sv, bin_inputs(a.ea, p, i));
             bin_done(a.ea, p, i, lane);
         }
         pos = seg_end;
@@ -361,13 +361,14 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
             continue;
         }
         const int i = b * 32 + lane;
+        float2 regs[15];  // this lane's per-bin values: the warp reduces its own group
         if (i < a.nbins) {
             double v[NV];
 #pragma unroll
             for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
-            bin_epilogue(a.ea, p, i, v);
+            bin_epilogue(a.ea, p, i, v, bin_inputs(a.ea, p, i), regs);
         }
-        group_done(a.ea, p, b, lane);
+        group_done(a.ea, p, b, lane, regs);
     }
     asm volatile("griddepcontrol.launch_dependents;");
 }

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_fused64_split(SplitArgs64 a) {
             double sv[NV];
 #pragma unroll
             for (int j = 0; j < NV; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
-            if (lane == 0) bin_epilogue(a.ea, p, i, sv);
+            if (lane == 0) bin_epilogue(a.ea, p, i, sv, bin_inputs(a.ea, p, i));
             bin_done(a.ea, p, i, lane);
         }
         pos = seg_end;
@@ -175,10 +175,9 @@ __global__ void __launch_bounds__(256) k_fused64_bins(BinArgs64 a) {
         const double2* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
         for (int k = 0; k < n; k++) m.update(g[(int64_t)k * 32], acc);
         const int i = b * 32 + lane;
-        if (i < a.nbins) {
-            bin_epilogue(a.ea, p, i, acc);
-        }
-        group_done(a.ea, p, b, lane);
+        float2 regs[15];  // this lane's per-bin values: the warp reduces its own group
+        if (i < a.nbins) bin_epilogue(a.ea, p, i, acc, bin_inputs(a.ea, p, i), regs);
+        group_done(a.ea, p, b, lane, regs);
     }
 }
 

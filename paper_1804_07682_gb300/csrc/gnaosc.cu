@@ -351,8 +351,9 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     // the kernel's constant term is wsum; the exact one is sum_r om_r when the
     // per-baseline sums carry the weight correction (or one baseline), else
     // sum_r (om_r + omlo_r)
-    ea.wsum_lo = (spec || plan->nl_inst == 1) ? plan->bc.wsum_lo : plan->wsum_all_lo;
-    for (int r = 0; r < GNA_NLMAX; r++) ea.om_delta[r] = (r < plan->nL) ? plan->bc.omd[r] - (double)plan->bc.om[r] : 0.0;
+    ea.wsum_lo = (float)((spec || plan->nl_inst == 1) ? plan->bc.wsum_lo : plan->wsum_all_lo);
+    for (int r = 0; r < GNA_NLMAX; r++)
+        ea.om_delta[r] = (r < plan->nL) ? (float)(plan->bc.omd[r] - (double)plan->bc.om[r]) : 0.f;
     ea.chi2 = q.chi2;
     ea.grad = q.grad;
     ea.H = q.H;
@@ -1035,8 +1036,8 @@ gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     return GNA_OK;
 }
 
-gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point, int reps,
-                             void* stream) {
+gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point,
+                             const gna_outputs* out, int reps, void* stream) {
     if (!plan || !params || !data) return GNA_EINVAL;
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1077,7 +1078,7 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    gna_outputs o{plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr};
+    const gna_outputs o = out ? *out : gna_outputs{plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr};
     for (const std::string& c : cand) {
         if (gna_plan_set_tuning(plan, c.c_str()) != GNA_OK) continue;
         gna_status st = gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);  // warm-up

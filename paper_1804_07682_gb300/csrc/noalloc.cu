@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256, 2) k_noalloc_chi2(NoAllocArgs a) {
             for (int j = 0; j < kNVT; j++) sv[j] = __shfl_sync(0xffffffffu, val, j);
             if (lane == 0) {
                 a.sumW[i] = sv[NV];
-                gna::bin_epilogue(a.ea, 0, i, sv);
+                gna::bin_epilogue(a.ea, 0, i, sv, gna::bin_inputs(a.ea, 0, i));
             }
             gna::bin_done(a.ea, 0, i, lane);
         }
@@ -227,7 +227,7 @@ extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, 
     ea.NBV = 5;
     ea.sumW = a.sumW;
     ea.shared_grid = 1;
-    ea.wsum_lo = (nl_inst == 1) ? bc.wsum_lo : fall - (double)bc.wsum;
+    ea.wsum_lo = (float)((nl_inst == 1) ? bc.wsum_lo : fall - (double)bc.wsum);
     ea.chi2 = chi2;
     ea.grad = grad;
     ea.gvals = reinterpret_cast<float2*>(base + kOffGrp);

@@ -199,6 +199,9 @@ __global__ void __launch_bounds__(256, GNA_SPLIT_MIN_BLOCKS) k_fused_split(Split
     gi += a.gstep;  // gi + 32 mod gn, with gi, gstep < gn
     if (gi >= gn) gi -= gn;
     float4 nx1 = __ldg(a.grid + gi);  // gi: grid index of f + 32
+    // a programmatic dependent of the kernel that prepares the per-point
+    // constants and zeroes the counters: wait (in hardware) for it here
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int64_t pos = f0; pos < f1;) {
         const int64_t q = pos / a.n;  // (point, bin) pair
         const int p = (int)(q / a.nbins);
@@ -303,6 +306,9 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
     const int lane = threadIdx.x & 31;
     int last_p = -1;
     M m;
+    // a programmatic dependent of the kernel that prepares the per-point
+    // constants and zeroes the counters: wait (in hardware) for it here
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     while (true) {
         int t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1);
@@ -373,16 +379,32 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// Launch as a programmatic dependent of the previous kernel in the stream
+// (the kernel preparing the constants): the node kernel's launch and block
+// placement overlap it; the kernel waits with griddepcontrol.wait.
+template <typename Kernel, typename Args>
+cudaError_t launch_dependent(Kernel k, const Args& a, int grid, int block, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 template <int PH, int NL, bool GRAD, bool SPEC>
 cudaError_t launch_split(const SplitArgs& a, int grid, int block, cudaStream_t s) {
-    k_fused_split<PH, NL, GRAD, SPEC><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(k_fused_split<PH, NL, GRAD, SPEC>, a, grid, block, s);
 }
 
 template <int PH, int NL, bool GRAD, bool SPEC>
 cudaError_t launch_bins(const BinArgs& a, int grid, int block, cudaStream_t s) {
-    k_fused_bins<PH, NL, GRAD, SPEC><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(k_fused_bins<PH, NL, GRAD, SPEC>, a, grid, block, s);
 }
 
 // Number of values per (point, bin) for the given flags.

@@ -321,11 +321,11 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
         ssh = slice_shape(plan);
         if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
     }
-    // work counter, per-point and per-bin arrival counters: one memset
+    // work counter, per-point and per-bin arrival counters: zeroed by the
+    // kernel that prepares the per-point constants
     const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups) +
                          (plan->mapping == MAP_SPLIT ? (int64_t)plan->npts * plan->nbins : 0);
-    CU(cudaMemsetAsync(plan->d_counters, 0, sizeof(int) * ncnt, s));
-    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s));
+    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s, plan->d_counters, ncnt));
     nl++;
     EpiArgs ea{};
     ea.is64 = plan->ph == 2;

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 #include "gnaosc.h"
+#include <algorithm>
+
 #include "misc.h"
 
 namespace gna {
@@ -16,9 +18,16 @@ namespace gna {
 // A21 = 4 s12 (1-s12)(1-s13)^2, A31 = 4 (1-s12)(1-s13) s13, A32 = 4 s12 (1-s13) s13
 // and their derivatives with respect to s12 = sin^2 theta12, s13 = sin^2 theta13;
 // the phase constants are c_ij,r = K dm2_ij L_r.  One thread per (point, baseline slot).
-__global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, BaseConst bc, PointConst* __restrict__ out) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = idx / GNA_NLMAX, r = idx % GNA_NLMAX;
+// Also zeroes the evaluation's nz counters (the node kernel that follows is a
+// programmatic dependent: it may be launched as soon as this kernel starts and
+// waits in hardware for its completion before touching counters or constants).
+__global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, BaseConst bc, PointConst* __restrict__ out,
+                                 int* __restrict__ zero, int64_t nz) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t k = tid; k < nz; k += (int64_t)gridDim.x * blockDim.x) zero[k] = 0;
+    const int64_t idx = tid;
+    const int p = (int)(idx / GNA_NLMAX), r = (int)(idx % GNA_NLMAX);
     if (p >= npts) return;
     const gna_osc o = prm[p];
     PointConst& pc = out[p];
@@ -53,9 +62,10 @@ __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, Base
     }
 }
 
-cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s) {
-    const int64_t threads = (int64_t)npts * GNA_NLMAX;
-    k_prepare_points<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, out);
+cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s,
+                           int* zero, int64_t nz) {
+    const int64_t threads = std::max<int64_t>((int64_t)npts * GNA_NLMAX, std::min<int64_t>(nz, 1LL << 20));
+    k_prepare_points<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, out, zero, nz);
     return cudaGetLastError();
 }
 

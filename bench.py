@@ -62,8 +62,8 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
 TRAFFIC_CAPTURE = {
     "split": {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
               "bytes": 265113600 + 4114176},
-    "slices": {"sources_sha256": "8e8935289b9e0d216520cc605b59e6d76225ef15d0e427ca459d34f7a962825d",
-               "bytes": 268566528 + 4605696 + 8175872},
+    "slices": {"sources_sha256": "b46c944c4bc17ec50e2ee604fb72594d4a5daec0ba2ab247bf9b300c13683f2f",
+               "bytes": 268521472 + 4717056 + 8175360},
 }
 KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
                   "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h",

@@ -318,7 +318,7 @@ def side_workloads(api, torch, device, args):
         ms = a0.elapsed_time(a1) / reps
         res[prec] = {"evals_per_s": 1e3 / ms, "us_per_eval": ms * 1e3, "tuning": plan.tuning}
         plan.close()
-    out["reactor_200x50"] = dict(res, note="10^4 nodes: launch-latency bound (graph replay of memset + 2 kernels)")
+    out["reactor_200x50"] = dict(res, note="10^4 nodes: launch-latency bound (graph replay of 2-3 kernels)")
     # the paper's Table 1 shape: bare OscProb in FP64 on 10^4 and 10^6 energies,
     # GPU compute only and with the host<->device transfers (the host side is
     # timed in the CPU-baseline leg)

@@ -188,6 +188,23 @@ gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const doub
                                const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
                                void* stream);
 
+/* gna_chain_eval_host_async / gna_chain_eval_host_wait: gna_chain_eval_host
+ * in two halves, so that consecutive evaluations overlap the host's packing,
+ * launching and unpacking with the device's work.  _async packs the inputs
+ * into one of the plan's two pinned staging slots, enqueues transfer ->
+ * evaluation -> transfer on `stream` (outputs: chi2, and the gradient and the
+ * spectra when grad / spectra != 0) and returns a ticket at once; _wait
+ * blocks until that evaluation is done and unpacks its results into the
+ * caller's buffers (any of them may be NULL).  At most two evaluations may be
+ * outstanding: _async returns GNA_ESTATE while the slot it needs holds a
+ * result not yet waited for, and _wait returns GNA_ESTATE for a ticket that
+ * is not outstanding.  The input buffers may be reused as soon as _async
+ * returns. */
+gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                                     const double* data, int data_per_point, int grad, int spectra, void* stream,
+                                     int64_t* ticket);
+gna_status gna_chain_eval_host_wait(gna_plan* plan, int64_t ticket, double* chi2, double* grad, double* spectra);
+
 /* gna_chain_eval_plain: the same outputs computed by the plain FP64 chain,
  * one kernel per transformation as in the paper (OscProb and its tangents ->
  * weight -> bin integration -> chi^2), intermediates in device memory, CUDA's

@@ -66,6 +66,9 @@ SIGNATURES = {
                                c_void_p]),
     "gna_chain_eval_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    "gna_chain_eval_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_int, c_int,
+                                          c_void_p, ctypes.POINTER(c_int64)]),
+    "gna_chain_eval_host_wait": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "gna_chain_eval_plain": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int,
                                      ctypes.POINTER(GnaOutputs), c_void_p]),
     "gna_fit_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p, c_int, c_void_p]),

@@ -224,6 +224,31 @@ class Plan:
         self._check(code, "gna_chain_eval_host")
         return c, g
 
+    def eval_host_async(self, params: np.ndarray, data: np.ndarray, eta: Optional[np.ndarray] = None,
+                        sigma: float = 0.0, grad: bool = True, spectra: bool = False, stream=None) -> int:
+        """Enqueues an evaluation from host buffers and returns a ticket at once
+        (at most two outstanding); eval_host_wait(ticket) takes its results."""
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.npts, 4)
+        d = np.ascontiguousarray(data, dtype=np.float64)
+        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        dpp = 1 if d.ndim == 2 else 0
+        vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+        t = ctypes.c_int64(-1)
+        code = self._lib.gna_chain_eval_host_async(self._h, vp(p), vp(e), float(sigma), vp(d), dpp, int(bool(grad)),
+                                                   int(bool(spectra)), ctypes.c_void_p(_stream(stream)), ctypes.byref(t))
+        self._check(code, "gna_chain_eval_host_async")
+        return t.value
+
+    def eval_host_wait(self, ticket: int, chi2_out: Optional[np.ndarray] = None, grad_out: Optional[np.ndarray] = None,
+                       spectra_out: Optional[np.ndarray] = None):
+        """Waits for the evaluation `ticket` and unpacks (chi2, grad) and, if given, the spectra."""
+        c = chi2_out if chi2_out is not None else np.empty(self.npts)
+        g = grad_out if grad_out is not None else np.empty((self.npts, 4))
+        vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+        code = self._lib.gna_chain_eval_host_wait(self._h, ctypes.c_int64(ticket), vp(c), vp(g), vp(spectra_out))
+        self._check(code, "gna_chain_eval_host_wait")
+        return c, g
+
     def fit(self, params: torch.Tensor, data: torch.Tensor, iters: int = 20, lambda0: float = 1e-3,
             graph: bool = True, chi2_out: Optional[torch.Tensor] = None, stream=None):
         """Batched Levenberg-Marquardt fits; params [npts, 4] is overwritten with the best points."""

@@ -151,13 +151,23 @@ struct gna_plan {
     int prof_n = 0;
     // packed staging of the host-buffer call: inputs [params | data | eta],
     // outputs [chi2 | grad | spectra], pinned on the host, contiguous on the device
-    double* h_in = nullptr;
-    double* h_out = nullptr;
+    // host-buffer evaluations: two pinned staging slots (an evaluation packs
+    // slot k while the one before it may still be copying from slot k ^ 1),
+    // one device staging pair (the stream serialises its use)
+    struct HostSlot {
+        double* h_in = nullptr;
+        double* h_out = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        GraphKey key;
+        cudaEvent_t done = nullptr;
+        int64_t ticket = -1;  // evaluation whose results the slot holds
+        bool pending = false; // enqueued, results not yet taken
+        bool grad = false, spectra = false;
+    } hs[2];
+    int64_t next_ticket = 0;
     double* d_in = nullptr;
     double* d_out = nullptr;
     size_t in_cap = 0, out_cap = 0;
-    cudaGraphExec_t hexec = nullptr;
-    GraphKey hkey;
     double* d_sumW = nullptr;  // [ngrids][nbins]
     double wsum_all_lo = 0.0;  // sum_r (om_r + omlo_r) - wsum: constant term when the weights enter as hi + lo
     // graphs are captured on a plan-owned stream joined to the caller's by events
@@ -428,6 +438,11 @@ void destroy_graph(gna_plan* p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
     p->gkey.v.clear();
+    for (auto& h : p->hs) {
+        if (h.exec) cudaGraphExecDestroy(h.exec);
+        h.exec = nullptr;
+        h.key.v.clear();
+    }
 }
 
 }  // namespace
@@ -495,9 +510,12 @@ gna_status gna_plan_destroy(gna_plan* plan) {
     if (!plan) return GNA_OK;
     destroy_graph(plan);
     destroy_profile(plan);
-    if (plan->hexec) cudaGraphExecDestroy(plan->hexec);
-    if (plan->h_in) cudaFreeHost(plan->h_in);
-    if (plan->h_out) cudaFreeHost(plan->h_out);
+    for (auto& h : plan->hs) {
+        if (h.exec) cudaGraphExecDestroy(h.exec);
+        if (h.done) cudaEventDestroy(h.done);
+        if (h.h_in) cudaFreeHost(h.h_in);
+        if (h.h_out) cudaFreeHost(h.h_out);
+    }
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     for (void* v : plan->allocs) cudaFree(v);
     delete plan;
@@ -717,10 +735,11 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     if ((int64_t)d->npts * d->nL * d->nbins <= (1LL << 24)) plan->out_cap += (size_t)d->npts * d->nL * d->nbins;
     TRY(dalloc(plan, &plan->d_in, plan->in_cap));
     TRY(dalloc(plan, &plan->d_out, plan->out_cap));
-    {
-        cudaError_t e1 = cudaMallocHost(&plan->h_in, plan->in_cap * sizeof(double));
-        cudaError_t e2 = cudaMallocHost(&plan->h_out, plan->out_cap * sizeof(double));
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    for (auto& h : plan->hs) {
+        cudaError_t e1 = cudaMallocHost(&h.h_in, plan->in_cap * sizeof(double));
+        cudaError_t e2 = cudaMallocHost(&h.h_out, plan->out_cap * sizeof(double));
+        cudaError_t e3 = cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
             cudaGetLastError();
             return fail(plan, GNA_ENOMEM, "pinned staging of %zu + %zu doubles", plan->in_cap, plan->out_cap);
         }
@@ -829,24 +848,29 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
     return GNA_OK;
 }
 
-gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
-                               const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
-                               void* stream) {
+gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                                     const double* data, int data_per_point, int grad, int spectra, void* stream,
+                                     int64_t* ticket) {
     if (!plan) return GNA_EINVAL;
-    if (!params || !data || !chi2) return fail(plan, GNA_EINVAL, "params, data and chi2 are required");
+    if (!params || !data || !ticket) return fail(plan, GNA_EINVAL, "params, data and ticket are required");
     if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
     const size_t n_spec = (size_t)plan->npts * plan->nL * plan->nbins;
     if (spectra && plan->out_cap < (size_t)plan->npts * 5 + n_spec)
         return fail(plan, GNA_ESHAPE, "spectra staging exceeds 2^24 values");
+    const int64_t t = plan->next_ticket;
+    auto& h = plan->hs[t & 1];
+    if (h.pending) return fail(plan, GNA_ESTATE, "two host evaluations are outstanding: wait for ticket %lld first", (long long)h.ticket);
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
+    // the slot's previous evaluation was taken; its copy from h_in is complete
+    CU(cudaEventSynchronize(h.done));
     // pack the inputs into pinned staging: [params | data | eta]
     const size_t n_par = (size_t)plan->npts * 4;
     const size_t n_dat = (data_per_point ? (size_t)plan->npts : 1) * plan->nbins;
     const size_t n_eta = eta ? (size_t)plan->nbins : 0;
-    memcpy(plan->h_in, params, n_par * sizeof(double));
-    memcpy(plan->h_in + n_par, data, n_dat * sizeof(double));
-    if (eta) memcpy(plan->h_in + n_par + n_dat, eta, n_eta * sizeof(double));
+    memcpy(h.h_in, params, n_par * sizeof(double));
+    memcpy(h.h_in + n_par, data, n_dat * sizeof(double));
+    if (eta) memcpy(h.h_in + n_par + n_dat, eta, n_eta * sizeof(double));
     const size_t n_in = n_par + n_dat + n_eta;
     const size_t n_out = (size_t)plan->npts * 5 + (spectra ? n_spec : 0);
     double* d_par = plan->d_in;
@@ -857,22 +881,22 @@ gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const doub
               spectra ? plan->d_out + (size_t)plan->npts * 5 : nullptr, nullptr};
     // one H2D, the evaluation, one D2H: replayed as one graph in graph mode
     auto enqueue_all = [&](cudaStream_t st, int* nl) -> gna_status {
-        CU(cudaMemcpyAsync(plan->d_in, plan->h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(plan->d_in, h.h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, st));
         TRY(enqueue_eval(plan, q, st, nl));
-        CU(cudaMemcpyAsync(plan->h_out, plan->d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(h.h_out, plan->d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
         return GNA_OK;
     };
     if (plan->use_graph) {
         double sig = sigma_eta;
         uintptr_t sigbits;
         memcpy(&sigbits, &sig, sizeof(sigbits));
-        GraphKey key{{(uintptr_t)data_per_point, (uintptr_t)(eta != nullptr), sigbits, (uintptr_t)(grad != nullptr),
-                      (uintptr_t)(spectra != nullptr), (uintptr_t)plan->block, (uintptr_t)plan->npt,
-                      (uintptr_t)plan->grid_mult}};
+        GraphKey key{{(uintptr_t)data_per_point, (uintptr_t)(eta != nullptr), sigbits, (uintptr_t)(grad != 0),
+                      (uintptr_t)(spectra != 0), (uintptr_t)plan->block, (uintptr_t)plan->npt,
+                      (uintptr_t)plan->grid_mult, (uintptr_t)plan->mapping, (uintptr_t)plan->slice_len}};
         cudaStream_t cs = plan->cap_stream;
-        if (!plan->hexec || !(key == plan->hkey)) {
-            if (plan->hexec) cudaGraphExecDestroy(plan->hexec);
-            plan->hexec = nullptr;
+        if (!h.exec || !(key == h.key)) {
+            if (h.exec) cudaGraphExecDestroy(h.exec);
+            h.exec = nullptr;
             CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             int nl = 0;
             gna_status st = enqueue_all(cs, &nl);
@@ -884,26 +908,53 @@ gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const doub
                 if (st != GNA_OK) return st;
                 return fail(plan, GNA_ECUDA, "host graph capture: %s", cudaGetErrorString(e));
             }
-            e = cudaGraphInstantiate(&plan->hexec, g, 0);
+            e = cudaGraphInstantiate(&h.exec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                plan->hexec = nullptr;
+                h.exec = nullptr;
                 return fail(plan, GNA_ECUDA, "host graph instantiate: %s", cudaGetErrorString(e));
             }
-            plan->hkey = key;
+            h.key = key;
             plan->graph_launches = nl;
         }
-        CU(cudaGraphLaunch(plan->hexec, s));
+        CU(cudaGraphLaunch(h.exec, s));
         plan->last_launches = plan->graph_launches;
     } else {
         TRY(enqueue_all(s, &plan->last_launches));
     }
-    CU(cudaStreamSynchronize(s));
-    memcpy(chi2, plan->h_out, sizeof(double) * plan->npts);
-    if (grad) memcpy(grad, plan->h_out + plan->npts, sizeof(double) * 4 * plan->npts);
-    if (spectra) memcpy(spectra, plan->h_out + (size_t)plan->npts * 5, sizeof(double) * n_spec);
+    CU(cudaEventRecord(h.done, s));
+    h.ticket = t;
+    h.pending = true;
+    h.grad = grad != 0;
+    h.spectra = spectra != 0;
+    plan->next_ticket = t + 1;
+    *ticket = t;
     return GNA_OK;
+}
+
+gna_status gna_chain_eval_host_wait(gna_plan* plan, int64_t ticket, double* chi2, double* grad, double* spectra) {
+    if (!plan) return GNA_EINVAL;
+    if (ticket < 0) return fail(plan, GNA_EINVAL, "bad ticket");
+    auto& h = plan->hs[ticket & 1];
+    if (h.ticket != ticket || !h.pending) return fail(plan, GNA_ESTATE, "no outstanding host evaluation %lld", (long long)ticket);
+    CU(cudaEventSynchronize(h.done));
+    h.pending = false;
+    if (chi2) memcpy(chi2, h.h_out, sizeof(double) * plan->npts);
+    if (grad && h.grad) memcpy(grad, h.h_out + plan->npts, sizeof(double) * 4 * plan->npts);
+    if (spectra && h.spectra) memcpy(spectra, h.h_out + (size_t)plan->npts * 5, sizeof(double) * plan->npts * plan->nL * plan->nbins);
+    return GNA_OK;
+}
+
+gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                               const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
+                               void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (!chi2) return fail(plan, GNA_EINVAL, "params, data and chi2 are required");
+    int64_t t = -1;
+    TRY(gna_chain_eval_host_async(plan, params, eta, sigma_eta, data, data_per_point, grad != nullptr, spectra != nullptr,
+                                  stream, &t));
+    return gna_chain_eval_host_wait(plan, t, chi2, grad, spectra);
 }
 
 gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,

@@ -241,6 +241,36 @@ def test_graph_replay_and_host_buffers(api):
     assert c[0] == a["chi2"][0].item() and np.array_equal(g, a["grad"].cpu().numpy())
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_host_evaluations_pipelined(api, graph):
+    # two outstanding host evaluations with different inputs, taken in order,
+    # give the same results as one synchronous call each; a third is refused
+    from paper_1804_07682_gb300 import _native as N
+    case = get_case("reactor8_40x3000")
+    w = case.w
+    plan = make_plan(api, case, "ff")
+    plan.set_graph(graph)
+    th0 = np.asarray(w.theta, dtype=np.float64).reshape(1, 4)
+    th1 = th0 * np.array([[1.01, 0.99, 1.02, 0.995]])
+    spec = np.empty((1, w.nL, w.nbins))
+    ref0 = plan.eval_host(th0, case.data, grad=True, spectra_out=spec.copy())  # same kernel as t0 (spectra on)
+    ref1 = plan.eval_host(th1, case.data, grad=True)
+    for _ in range(3):
+        t0 = plan.eval_host_async(th0, case.data, grad=True, spectra=True)
+        t1 = plan.eval_host_async(th1, case.data, grad=True)
+        with pytest.raises(N.GnaError):
+            plan.eval_host_async(th0, case.data)
+        c0, g0 = plan.eval_host_wait(t0, spectra_out=spec)
+        with pytest.raises(N.GnaError):
+            plan.eval_host_wait(t0)
+        c1, g1 = plan.eval_host_wait(t1)
+        assert c0[0] == ref0[0][0] and np.array_equal(g0, ref0[1])
+        assert c1[0] == ref1[0][0] and np.array_equal(g1, ref1[1])
+    ref = case.oracle_point(0)
+    assert rel(spec[0], ref["mu_rb"]) < 1e-6
+    plan.close()
+
+
 def test_autotune_keeps_parity(api):
     case = get_case("reactor8_40x3000")
     w = case.w

@@ -353,6 +353,26 @@ def side_workloads(api, torch, device, args):
         gpu_xfer_ms = (time.perf_counter() - t0) * 1e3 / reps
         t1[str(n)] = {"gpu_compute_ms": gpu_ms, "gpu_with_transfer_ms": gpu_xfer_ms}
     out["oscprob_fp64_table1_shape"] = t1
+    # any channel (general formula with the CP term): numu -> nue and numu ->
+    # numu at 810 km on 10^6 energies in 0.5-5 GeV, FP64 and mixed
+    gen = {}
+    th_full = (wl.TRUTH[0], wl.TRUTH[1], 0.545, 1.2 * np.pi, wl.TRUTH[2], wl.TRUTH[3])
+    E_d = torch.linspace(500.0, 5000.0, 10 ** 6, dtype=torch.float64, device=device)
+    for a, b in (("mu", "e"), ("mu", "mu")):
+        for prec in ("fp64", "ff"):
+            for _ in range(5):
+                api.oscprob_general(E_d, [810.0], th_full, a, b, prec=prec)
+            torch.cuda.synchronize()
+            reps = 200
+            a0, a1 = ev(), ev()
+            a0.record(stream)
+            for _ in range(reps):
+                api.oscprob_general(E_d, [810.0], th_full, a, b, prec=prec)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms = a0.elapsed_time(a1) / reps
+            gen["%s->%s %s" % (a, b, prec)] = {"us": ms * 1e3, "gpoints_per_s": 1e6 / (ms * 1e-3) / 1e9}
+    out["oscprob_any_channel_810km_1e6"] = gen
     return out
 
 

@@ -102,6 +102,13 @@ typedef struct {
     double* spectra; /* [npts][nL][nbins] per-baseline integrals mu_r,i = int_bin S(E) P_r(E) dE */
 } gna_outputs;
 
+/* Parameters of the general three-flavour formula (gna_oscprob, gna_pmns). */
+typedef struct {
+    double s2_12, s2_13, s2_23; /* sin^2 theta12, theta13, theta23 */
+    double delta_cp;            /* CP phase, rad */
+    double dm2_21, dm2_32;      /* eV^2; dm2_31 = dm2_21 + dm2_32 (normal ordering) */
+} gna_osc_full;
+
 typedef struct gna_plan gna_plan;
 
 /* ---------------------------------------------------------------------------
@@ -132,6 +139,30 @@ gna_status gna_gl_nodes(int n, double* x, double* w, void* stream);
  */
 gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p,
                           gna_precision prec, void* P_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gna_pmns: the mixing matrix U[alpha][i] (alpha = e, mu, tau; i = 1, 2, 3)
+ * in the standard parameterisation (paper Sec. 4.1 uses its elements),
+ * U = R23 U13(delta) R12, as row-major real and imaginary parts [9] each.
+ * Host only (no device work).  GNA_EINVAL for NULL pointers or s2 outside [0, 1].
+ */
+gna_status gna_pmns(const gna_osc_full* p, double* U_re, double* U_im);
+
+/* ---------------------------------------------------------------------------
+ * gna_oscprob: element-wise OscProb for any channel, paper Sec. 4.1 (the
+ * general formula with its Im term):
+ *   P[r][k] = delta_ab + sum_{i>j} [-4 Re X_ij sin^2 x_ij + 2 Im X_ij sin 2x_ij],
+ *   X_ij = V*_ai V_bi V_aj V*_bj, V = U for neutrinos (anti = 0) and U* for
+ *   antineutrinos (anti = 1), x_ij = K dm2_ij L[r] / E[k].
+ *   alpha, beta: 0 = e, 1 = mu, 2 = tau
+ *   E, L, prec, P_out, n, nL: as for gna_oscprob_ee
+ * The mixed precisions reduce each phase modulo pi (both sin^2 x and sin 2x
+ * have that period) and evaluate FP32 polynomials; P is then accurate to
+ * ~1e-7 absolute.  GNA_EINVAL for a flavour outside 0..2, NULL pointers or
+ * an unknown precision; GNA_ESHAPE for n < 0 or bad nL.
+ */
+gna_status gna_oscprob(const double* E, int64_t n, const double* L, int nL, int alpha, int beta, int anti,
+                       const gna_osc_full* p, gna_precision prec, void* P_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * gna_plan_create: configuration stage (paper Sec. 2, Sec. 4.2): validates

@@ -27,6 +27,11 @@ class GnaOsc(ctypes.Structure):
     _fields_ = [("s2_12", c_double), ("s2_13", c_double), ("dm2_21", c_double), ("dm2_32", c_double)]
 
 
+class GnaOscFull(ctypes.Structure):
+    _fields_ = [("s2_12", c_double), ("s2_13", c_double), ("s2_23", c_double), ("delta_cp", c_double),
+                ("dm2_21", c_double), ("dm2_32", c_double)]
+
+
 class GnaPlanDesc(ctypes.Structure):
     _fields_ = [
         ("nbins", c_int),
@@ -55,6 +60,9 @@ class GnaOutputs(ctypes.Structure):
 SIGNATURES = {
     "gna_strerror": (c_char_p, [c_int]),
     "gna_gl_nodes": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
+    "gna_pmns": (c_int, [ctypes.POINTER(GnaOscFull), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "gna_oscprob": (c_int, [c_void_p, c_int64, ctypes.POINTER(c_double), c_int, c_int, c_int, c_int,
+                            ctypes.POINTER(GnaOscFull), c_int, c_void_p, c_void_p]),
     "gna_oscprob_ee": (c_int, [c_void_p, c_int64, ctypes.POINTER(c_double), c_int, ctypes.POINTER(GnaOsc), c_int,
                                c_void_p, c_void_p]),
     "gna_plan_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(GnaPlanDesc), c_void_p]),

@@ -67,6 +67,39 @@ def oscprob(E: torch.Tensor, L: Sequence[float], theta: Sequence[float], prec: s
     return P
 
 
+FLAVOURS = {"e": 0, "mu": 1, "tau": 2}
+
+
+def pmns(theta_full: Sequence[float]) -> np.ndarray:
+    """Mixing matrix U[alpha][i] (complex 3x3, host) for (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32)."""
+    p = N.GnaOscFull(*[float(t) for t in theta_full])
+    re = np.empty(9)
+    im = np.empty(9)
+    P = ctypes.POINTER(ctypes.c_double)
+    N.check(N.lib().gna_pmns(ctypes.byref(p), re.ctypes.data_as(P), im.ctypes.data_as(P)), what="gna_pmns")
+    return (re + 1j * im).reshape(3, 3)
+
+
+def oscprob_general(E: torch.Tensor, L: Sequence[float], theta_full: Sequence[float], alpha="mu", beta="e",
+                    anti: bool = False, prec: str = "fp64") -> torch.Tensor:
+    """Element-wise OscProb for any channel: P(alpha -> beta) [nL, n] at energies E (MeV) for
+    baselines L (km); theta_full = (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32)."""
+    _require_cuda()
+    if E.dtype != torch.float64:
+        raise ValueError("E must be float64")
+    a = FLAVOURS.get(alpha, alpha)
+    b = FLAVOURS.get(beta, beta)
+    Ls = _f64(L)
+    p = N.GnaOscFull(*[float(t) for t in theta_full])
+    out_dtype = torch.float64 if prec == "fp64" else torch.float32
+    P = torch.empty((Ls.size, E.numel()), dtype=out_dtype, device=E.device)
+    code = N.lib().gna_oscprob(_ptr(E.contiguous()), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               Ls.size, int(a), int(b), int(bool(anti)), ctypes.byref(p), PRECISIONS[prec], _ptr(P),
+                               ctypes.c_void_p(_stream()))
+    N.check(code, what="gna_oscprob")
+    return P
+
+
 class Plan:
     """A configured chain (paper's configuration stage): energy grids built and
     all scratch allocated on the device; evaluations only launch kernels."""

@@ -193,3 +193,17 @@ __host__ __device__ __forceinline__ void split_ff(double x, float& hi, float& lo
     hi = (float)x;
     lo = (float)(x - (double)hi);
 }
+
+// 1 / E as a float pair without an FP64 division (FP64 runs at 1/64 of the
+// FP32 rate here): r = rcp(E_hi), then one Newton-Raphson step carried in
+// double-float, 1/E = r / (1 - e) = r (1 + e + e^2 ...), e = 1 - E r, whose
+// leading part 1 - E_hi r the FMA forms exactly.  Relative error ~e^2 < 2^-44.
+__device__ __forceinline__ void ff_recip(double E, float& rh, float& rl) {
+    float eh, el;
+    split_ff(E, eh, el);
+    const float r = __frcp_rn(eh);
+    const float e = fmaf(-el, r, fmaf(-eh, r, 1.0f));
+    const float lo = r * e;
+    rh = r + lo;
+    rl = lo - (rh - r);
+}

@@ -5,6 +5,7 @@
 // inputs are views, two host/device transfers per sub-chain, GPU status
 // readable on the host).
 #include <algorithm>
+#include <complex>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -503,6 +504,67 @@ gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, c
         split_ff(oc.c21[r] + oc.c32[r], oc.c31h[r], oc.c31l[r]);
     }
     cudaError_t e = launch_oscprob(E, n, oc, prec, P_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
+}
+
+gna_status gna_pmns(const gna_osc_full* p, double* U_re, double* U_im) {
+    if (!p || !U_re || !U_im) return GNA_EINVAL;
+    const double q[3] = {p->s2_12, p->s2_13, p->s2_23};
+    for (double v : q)
+        if (!(v >= 0.0 && v <= 1.0)) return GNA_EINVAL;
+    // elements of R23 U13(delta) R12 written out (s_ij = sin, c_ij = cos)
+    const double s12 = std::sqrt(q[0]), c12 = std::sqrt(1.0 - q[0]);
+    const double s13 = std::sqrt(q[1]), c13 = std::sqrt(1.0 - q[1]);
+    const double s23 = std::sqrt(q[2]), c23 = std::sqrt(1.0 - q[2]);
+    const std::complex<double> ed = std::polar(1.0, p->delta_cp);  // e^{i delta}
+    const std::complex<double> U[3][3] = {
+        {c12 * c13, s12 * c13, s13 * std::conj(ed)},
+        {-s12 * c23 - c12 * s23 * s13 * ed, c12 * c23 - s12 * s23 * s13 * ed, s23 * c13},
+        {s12 * s23 - c12 * c23 * s13 * ed, -c12 * s23 - s12 * c23 * s13 * ed, c23 * c13}};
+    for (int a = 0; a < 3; a++)
+        for (int i = 0; i < 3; i++) {
+            U_re[3 * a + i] = U[a][i].real();
+            U_im[3 * a + i] = U[a][i].imag();
+        }
+    return GNA_OK;
+}
+
+gna_status gna_oscprob(const double* E, int64_t n, const double* L, int nL, int alpha, int beta, int anti,
+                       const gna_osc_full* p, gna_precision prec, void* P_out, void* stream) {
+    if (n < 0 || nL < 1 || nL > GNA_NLMAX) return GNA_ESHAPE;
+    if (!L || !p || alpha < 0 || alpha > 2 || beta < 0 || beta > 2) return GNA_EINVAL;
+    if (prec != GNA_FP64 && prec != GNA_MIXED_F64PHASE && prec != GNA_MIXED_FFPHASE) return GNA_EINVAL;
+    double ure[9], uim[9];
+    if (gna_pmns(p, ure, uim) != GNA_OK) return GNA_EINVAL;
+    if (n == 0) return GNA_OK;
+    if (!E || !P_out) return GNA_EINVAL;
+    // V = U or U*; X_ij = V*_ai V_bi V_aj V*_bj for (i, j) = (2, 1), (3, 1), (3, 2)
+    auto V = [&](int a, int i) {
+        return std::complex<double>(ure[3 * a + i], anti ? -uim[3 * a + i] : uim[3 * a + i]);
+    };
+    const int pi_[3] = {1, 2, 2}, pj_[3] = {0, 0, 1};
+    OscGenConst oc{};
+    oc.nL = nL;
+    oc.dab = (alpha == beta) ? 1.0 : 0.0;
+    for (int q = 0; q < 3; q++) {
+        const int i = pi_[q], j = pj_[q];
+        const std::complex<double> X = std::conj(V(alpha, i)) * V(beta, i) * V(alpha, j) * std::conj(V(beta, j));
+        oc.cr[q] = -4.0 * X.real();
+        oc.ci[q] = 2.0 * X.imag();
+        oc.crf[q] = (float)oc.cr[q];
+        oc.cif[q] = (float)oc.ci[q];
+    }
+    for (int r = 0; r < nL; r++) {
+        if (!(L[r] >= 0.0)) return GNA_EINVAL;
+        const double kl = GNA_K_PHASE * L[r];
+        const double c21 = p->dm2_21 * kl, c32 = p->dm2_32 * kl;
+        const double cq[3] = {c21, c21 + c32, c32};
+        for (int q = 0; q < 3; q++) {
+            oc.c[q][r] = cq[q];
+            split_ff(cq[q], oc.ch[q][r], oc.cl[q][r]);
+        }
+    }
+    cudaError_t e = launch_oscgen(E, n, oc, prec, P_out, (cudaStream_t)stream);
     return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
 }
 

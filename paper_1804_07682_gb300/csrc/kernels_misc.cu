@@ -343,9 +343,9 @@ template <int PH>
 __global__ void k_oscprob_mixed(const double* __restrict__ E, int64_t n, OscConst oc, float* __restrict__ P) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const double ed = 1.0 / E[k];
     float eh, el;
-    split_ff(ed, eh, el);
+    ff_recip(E[k], eh, el);
+    const double ed = (double)eh + (double)el;
     const float A21 = oc.Af[0], A31 = oc.Af[1], A32 = oc.Af[2];
     const float omA21 = oc.one_minus_A21f;
     for (int r = 0; r < oc.nL; r++) {

@@ -36,6 +36,18 @@ struct OscConst {
     int nL;
 };
 
+// Constants of the general-channel kernel: phases q = (21, 31, 32) per
+// baseline (double and hi + lo floats), coefficients -4 Re X and 2 Im X.
+struct OscGenConst {
+    double c[3][GNA_NLMAX];
+    float ch[3][GNA_NLMAX], cl[3][GNA_NLMAX];
+    double cr[3], ci[3];
+    float crf[3], cif[3];
+    double dab;  // delta_ab
+    int nL;
+};
+cudaError_t launch_oscgen(const double* E, int64_t n, const OscGenConst& oc, int prec, void* P, cudaStream_t s);
+
 struct LMState {
     double best[4];
     double chi2;

@@ -78,6 +78,54 @@ def test_oscprob_edge_cases(api):
     assert api.oscprob(dev(np.zeros(0)), [1.0], wl.TRUTH, "fp64").numel() == 0
 
 
+# ------------------------------------------------- OscProb, any channel
+THETA_FULL = (0.307, 0.0218, 0.545, 1.2 * np.pi, 7.53e-5, 2.44e-3)
+FL = {"e": 0, "mu": 1, "tau": 2}
+
+
+def oracle_prob(a, b, E, L, anti, th=THETA_FULL):
+    s12, s13, s23, d, dm21, dm32 = th
+    return np.array([oracle.prob(FL[a], FL[b], s12, s13, s23, d, dm21, dm32, L, e, anti) for e in E])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
+@pytest.mark.parametrize("anti", [False, True])
+@pytest.mark.parametrize("a,b", [("e", "e"), ("mu", "mu"), ("mu", "e"), ("e", "tau"), ("tau", "mu")])
+def test_oscprob_general(api, prec, anti, a, b):
+    # long-baseline energies (0.5-5 GeV) at 810 and 295 km, the Im (CP) term on
+    rng = np.random.default_rng(5)
+    E = rng.uniform(500.0, 5000.0, 1537)
+    L = [810.0, 295.0]
+    P = api.oscprob_general(dev(E), L, THETA_FULL, a, b, anti=anti, prec=prec).double().cpu().numpy()
+    for r, Lr in enumerate(L):
+        ref = oracle_prob(a, b, E, Lr, anti)
+        err = np.abs(P[r] - ref).max()
+        assert err < (1e-12 if prec == "fp64" else 3e-7), (prec, a, b, anti, Lr, err)
+
+
+def test_oscprob_general_identities(api):
+    rng = np.random.default_rng(6)
+    E = dev(rng.uniform(200.0, 8000.0, 4099))
+    L = [810.0, 52.5, 0.0]
+    P = {(a, b, anti): api.oscprob_general(E, L, THETA_FULL, a, b, anti=anti).cpu().numpy()
+         for a in FL for b in FL for anti in (False, True)}
+    for anti in (False, True):
+        for a in FL:  # unitarity: rows and columns sum to one
+            assert np.abs(sum(P[(a, b, anti)] for b in FL) - 1.0).max() < 1e-12
+            assert np.abs(sum(P[(b, a, anti)] for b in FL) - 1.0).max() < 1e-12
+    for a in FL:  # CPT: P(a -> b, antineutrino) = P(b -> a, neutrino)
+        for b in FL:
+            assert np.abs(P[(a, b, True)] - P[(b, a, False)]).max() < 1e-13
+            assert np.all(P[(a, b, False)][2] == (1.0 if a == b else 0.0))  # L = 0
+    # nue_bar survival from the general kernel equals the dedicated one
+    th4 = (THETA_FULL[0], THETA_FULL[1], THETA_FULL[4], THETA_FULL[5])
+    Pee = api.oscprob(E, L, th4, "fp64").cpu().numpy()
+    assert np.abs(P[("e", "e", True)] - Pee).max() < 1e-13
+    from paper_1804_07682_gb300 import _native as N
+    with pytest.raises(N.GnaError):
+        api.oscprob_general(E, L, THETA_FULL, 3, 0)
+
+
 # ------------------------------------------------------- chain, small cases
 def small_cases():
     return {

@@ -206,6 +206,22 @@ gna_status gna_plan_info(const gna_plan* plan, int64_t* nodes, int64_t* points_p
 gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
                           const double* data, int data_per_point, const gna_outputs* out, void* stream);
 
+/* gna_chain_eval_cached: the epilogue only (steps a7-a9: nuisance
+ * normalisation, chi^2, gradient contraction) on the per-bin node sums that
+ * the plan's last gna_chain_eval / host-buffer evaluation kept, with new
+ * eta, sigma_eta and data: the oscillation parameters are that
+ * evaluation's.  This is the paper's recompute-only-what-changed rule for
+ * the transformations downstream of the node pass (Sec. 2: a transformation
+ * is recomputed only when its inputs change); a nuisance or data change costs
+ * O(npts x nbins) work instead of a pass over the nodes.  Outputs as for
+ * gna_chain_eval; grad / grad_eta need a kept evaluation with a gradient,
+ * spectra one with spectra (else GNA_ESTATE, also when none was kept yet);
+ * GNA_ESHAPE when the plan keeps no sums (npts x nbins x values > 2^25).
+ * Stream order: enqueue after the evaluation that kept the sums (same stream,
+ * or synchronise). */
+gna_status gna_chain_eval_cached(gna_plan* plan, const double* eta, double sigma_eta, const double* data,
+                                 int data_per_point, const gna_outputs* out, void* stream);
+
 /* gna_chain_eval_host: the same evaluation from HOST buffers (the paper's
  * Sec. 4.2 sub-chain with one transfer in and one out): packs params [npts],
  * data and eta [nbins] (or NULL) into the plan's pinned staging, copies them

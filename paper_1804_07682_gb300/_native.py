@@ -72,6 +72,8 @@ SIGNATURES = {
     "gna_plan_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
     "gna_chain_eval": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, ctypes.POINTER(GnaOutputs),
                                c_void_p]),
+    "gna_chain_eval_cached": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_int, ctypes.POINTER(GnaOutputs),
+                                      c_void_p]),
     "gna_chain_eval_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
     "gna_chain_eval_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_int, c_int,

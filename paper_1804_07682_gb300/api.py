@@ -241,6 +241,31 @@ class Plan:
         self._check(code, "gna_chain_eval_plain" if plain else "gna_chain_eval")
         return out
 
+    def eval_cached(self, data: torch.Tensor, eta: Optional[torch.Tensor] = None, sigma: float = 0.0,
+                    grad: bool = True, grad_eta: bool = False, mu: bool = False, spectra: bool = False,
+                    out: Optional[dict] = None, stream=None) -> dict:
+        """The epilogue only (nuisances, chi^2, gradient) on the node sums the last
+        evaluation kept: new eta / data, the same oscillation parameters."""
+        dpp = 1 if data.dim() == 2 else 0
+        if data.dtype != torch.float64 or data.shape[-1] != self.nbins or (dpp and data.shape[0] != self.npts):
+            raise ValueError("data must be float64 [nbins] or [npts, nbins]")
+        if out is None:
+            out = {"chi2": self._out("chi2", (self.npts,))}
+            if grad:
+                out["grad"] = self._out("grad", (self.npts, 4))
+            if grad_eta:
+                out["grad_eta"] = self._out("grad_eta", (self.npts, self.nbins))
+            if mu:
+                out["mu"] = self._out("mu", (self.npts, self.nbins))
+            if spectra:
+                out["spectra"] = self._out("spectra", (self.npts, self.nL, self.nbins))
+        o = N.GnaOutputs(_ptr(out["chi2"]), _ptr(out.get("grad")), _ptr(out.get("grad_eta")), _ptr(out.get("mu")),
+                         _ptr(out.get("spectra")))
+        code = self._lib.gna_chain_eval_cached(self._h, _ptr(eta), float(sigma), _ptr(data), dpp, ctypes.byref(o),
+                                               ctypes.c_void_p(_stream(stream)))
+        self._check(code, "gna_chain_eval_cached")
+        return out
+
     def eval_host(self, params: np.ndarray, data: np.ndarray, eta: Optional[np.ndarray] = None, sigma: float = 0.0,
                   grad: bool = True, chi2_out: Optional[np.ndarray] = None, grad_out: Optional[np.ndarray] = None,
                   spectra_out: Optional[np.ndarray] = None, stream=None):

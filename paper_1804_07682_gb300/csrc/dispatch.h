@@ -14,4 +14,6 @@ int split_regs(int ph, int nl, bool grad, bool spec);
 // (point, group) in part [npts][ngroups][S][NV][32]
 struct EpiArgs;
 cudaError_t launch_slices_reduce(const float2* part, int S, int NV, const EpiArgs& ea, int npts, cudaStream_t s);
+// epilogue only, on kept node sums [npts][nbins][ea.NV] (slices.cu)
+cudaError_t launch_cached_epilogue(const double* sums, const EpiArgs& ea, cudaStream_t s);
 }  // namespace gna

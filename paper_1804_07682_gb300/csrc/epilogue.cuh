@@ -54,6 +54,7 @@ struct EpiArgs {
     int* pt_cnt;           // [npts] groups finished, zeroed before the launch
     int* grp_cnt;          // [npts][ngroups] bins finished, zeroed before the launch
     int* bin_cnt;          // [npts][nbins] segments finished (split mapping), zeroed before the launch
+    double* binsums;       // [npts][nbins][NV] node sums kept for epilogue-only re-evaluations, or NULL
 };
 
 __device__ __forceinline__ float2 to_ff(double x) {
@@ -97,6 +98,8 @@ __device__ __forceinline__ BinIn bin_inputs(const EpiArgs& a, int p, int i) {
 __device__ inline void bin_epilogue(const EpiArgs& a, int p, int i, const double* v, const BinIn& in,
                                     float2* regs = nullptr) {
     const int64_t idx = (int64_t)p * a.nbins + i;
+    if (a.binsums)
+        for (int j = 0; j < a.NV; j++) a.binsums[idx * a.NV + j] = v[j];
     double M = v[0];
     const int off = 1 + (a.has_grad ? 4 : 0);
     if (!a.is64) {

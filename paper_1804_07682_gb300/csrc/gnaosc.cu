@@ -120,6 +120,9 @@ struct gna_plan {
     size_t part_cap = 0;  // elements of 8 bytes
     float2* d_binvals = nullptr;
     float2* d_gvals = nullptr;  // [npts][ngroups][15] group sums
+    // per-bin node sums of the last evaluation, for epilogue-only re-evaluations
+    double* d_binsums = nullptr;  // [npts][nbins][nv_max], or NULL (too large)
+    bool cache_valid = false, cache_grad = false, cache_spec = false;
     double* d_H = nullptr;
     double* d_chi2_tmp = nullptr;
     double* d_grad_tmp = nullptr;
@@ -314,30 +317,9 @@ struct EvalReq {
     double* H;  // [npts][10] or NULL (fitter)
 };
 
-// Enqueue one fused evaluation; counts kernel launches into *launches.
-gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* launches) {
-    const bool grad = q.grad || q.grad_eta || q.H;
-    const bool spec = q.spectra != nullptr;
-    int nl = 0;
-    const int NV = value_count(plan, grad, spec);
-    SplitShape sh{};
-    if (plan->mapping == MAP_SPLIT) {
-        sh = split_shape(plan, grad, spec);
-        if ((size_t)plan->npts * plan->nbins * sh.maxseg * NV > plan->part_cap)
-            return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
-                        (long long)plan->npts * plan->nbins * sh.maxseg * NV, plan->part_cap);
-    }
-    SliceShape ssh{1, 0, plan->ntasks};
-    if (plan->mapping == MAP_SLICES) {
-        ssh = slice_shape(plan);
-        if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
-    }
-    // work counter, per-point and per-bin arrival counters: zeroed by the
-    // kernel that prepares the per-point constants
-    const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups) +
-                         (plan->mapping == MAP_SPLIT ? (int64_t)plan->npts * plan->nbins : 0);
-    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s, plan->d_counters, ncnt));
-    nl++;
+// Epilogue arguments of one evaluation (outputs of q; NV node sums per bin
+// laid out for the grad / spec flags).
+EpiArgs make_epi(const gna_plan* plan, const EvalReq& q, bool grad, bool spec, int NV) {
     EpiArgs ea{};
     ea.is64 = plan->ph == 2;
     ea.NV = NV;
@@ -373,6 +355,36 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     ea.pt_cnt = plan->d_counters + 1;
     ea.grp_cnt = plan->d_counters + 1 + plan->npts;
     ea.bin_cnt = plan->d_counters + 1 + plan->npts + (int64_t)plan->npts * plan->ngroups;
+    return ea;
+}
+
+// Enqueue one fused evaluation; counts kernel launches into *launches.
+gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* launches) {
+    const bool grad = q.grad || q.grad_eta || q.H;
+    const bool spec = q.spectra != nullptr;
+    int nl = 0;
+    const int NV = value_count(plan, grad, spec);
+    SplitShape sh{};
+    if (plan->mapping == MAP_SPLIT) {
+        sh = split_shape(plan, grad, spec);
+        if ((size_t)plan->npts * plan->nbins * sh.maxseg * NV > plan->part_cap)
+            return fail(plan, GNA_ESHAPE, "launch shape needs %lld partials, capacity %zu",
+                        (long long)plan->npts * plan->nbins * sh.maxseg * NV, plan->part_cap);
+    }
+    SliceShape ssh{1, 0, plan->ntasks};
+    if (plan->mapping == MAP_SLICES) {
+        ssh = slice_shape(plan);
+        if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
+    }
+    // work counter, per-point and per-bin arrival counters: zeroed by the
+    // kernel that prepares the per-point constants
+    const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups) +
+                         (plan->mapping == MAP_SPLIT ? (int64_t)plan->npts * plan->nbins : 0);
+    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s, plan->d_counters, ncnt));
+    nl++;
+    EpiArgs ea = make_epi(plan, q, grad, spec, NV);
+    // keep the node sums for epilogue-only re-evaluations (not in fits)
+    ea.binsums = q.H ? nullptr : plan->d_binsums;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(s, &cap));
     const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
@@ -415,6 +427,11 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     if (timed) {
         CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n + 1], s));
         plan->prof_n++;
+    }
+    if (ea.binsums) {
+        plan->cache_valid = true;
+        plan->cache_grad = grad;
+        plan->cache_spec = spec;
     }
     *launches = nl;
     return GNA_OK;
@@ -789,6 +806,8 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     }
     TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
     TRY(dalloc(plan, &plan->d_gvals, (size_t)d->npts * ngroups * 15));
+    if ((int64_t)d->npts * d->nbins * nv_max <= (32LL << 20))  // up to 256 MB
+        TRY(dalloc(plan, &plan->d_binsums, (size_t)d->npts * d->nbins * nv_max));
     TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
     TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
     TRY(dalloc(plan, &plan->d_grad_tmp, (size_t)d->npts * 4));
@@ -907,6 +926,31 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
     // captured on the plan's own stream, replayed on the caller's
     CU(cudaGraphLaunch(plan->gexec, s));
     plan->last_launches = plan->graph_launches;
+    return GNA_OK;
+}
+
+gna_status gna_chain_eval_cached(gna_plan* plan, const double* eta, double sigma_eta, const double* data,
+                                 int data_per_point, const gna_outputs* out, void* stream) {
+    if (!plan || !out || !out->chi2 || !data) return GNA_EINVAL;
+    if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
+    if (!plan->d_binsums) return fail(plan, GNA_ESHAPE, "the plan keeps no node sums (points x bins too large)");
+    if (!plan->cache_valid) return fail(plan, GNA_ESTATE, "no evaluation has kept node sums yet");
+    if ((out->grad || out->grad_eta) && !plan->cache_grad)
+        return fail(plan, GNA_ESTATE, "the kept node sums have no tangents (evaluate with a gradient first)");
+    if (out->spectra && !plan->cache_spec)
+        return fail(plan, GNA_ESTATE, "the kept node sums have no per-baseline spectra");
+    if (out->grad_eta && !eta) return fail(plan, GNA_EINVAL, "grad_eta needs eta");
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    const int NV = value_count(plan, plan->cache_grad, plan->cache_spec);
+    EvalReq q{nullptr, eta, sigma_eta, data, data_per_point, out->chi2, out->grad, out->grad_eta, out->mu, out->spectra,
+              nullptr};
+    EpiArgs ea = make_epi(plan, q, plan->cache_grad, plan->cache_spec, NV);
+    ea.NBV = out->grad ? 5 : 1;  // the tangent terms are summed over bins only when asked for
+    ea.binsums = nullptr;
+    CU(cudaMemsetAsync(plan->d_counters, 0, sizeof(int) * (1 + (size_t)plan->npts * (1 + plan->ngroups)), s));
+    CU(launch_cached_epilogue(plan->d_binsums, ea, s));
+    plan->last_launches = 1;
     return GNA_OK;
 }
 

@@ -101,4 +101,29 @@ cudaError_t launch_slices_reduce(const float2* part, int S, int NV, const EpiArg
     return launch_reduce<kMaxNV, 16>(part, S, NV, ea, npts, s);
 }
 
+// Epilogue-only evaluation (steps a7-a9) on the node sums a previous
+// evaluation kept: one warp per (point, group of 32 bins), lane l bin 32 g + l.
+__global__ void __launch_bounds__(256) k_cached_epilogue(const double* __restrict__ sums, EpiArgs ea) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)ea.npts * ea.ngroups) return;
+    const int p = (int)(wid / ea.ngroups);
+    const int g = (int)(wid - (int64_t)p * ea.ngroups);
+    const int i = g * 32 + lane;
+    float2 regs[15];
+    if (i < ea.nbins) {
+        double v[kMaxNV];
+        const double* src = sums + ((int64_t)p * ea.nbins + i) * ea.NV;
+        for (int j = 0; j < ea.NV; j++) v[j] = src[j];
+        bin_epilogue(ea, p, i, v, bin_inputs(ea, p, i), regs);
+    }
+    group_done(ea, p, g, lane, regs);
+}
+
+cudaError_t launch_cached_epilogue(const double* sums, const EpiArgs& ea, cudaStream_t s) {
+    const int64_t threads = (int64_t)ea.npts * ea.ngroups * 32;
+    k_cached_epilogue<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(sums, ea);
+    return cudaGetLastError();
+}
+
 }  // namespace gna

@@ -319,6 +319,41 @@ def test_host_evaluations_pipelined(api, graph):
     plan.close()
 
 
+@pytest.mark.parametrize("mapping", ["split", "bins", "slices"])
+def test_cached_epilogue_matches_full_evaluation(api, mapping):
+    # new nuisances and new data on the kept node sums give exactly what a
+    # full evaluation with them gives (same sums, same epilogue)
+    from paper_1804_07682_gb300 import _native as N
+    case = get_case("nuisance_64x1000")
+    w = case.w
+    plan = make_plan(api, case, "ff", mapping)
+    p = plan.params_tensor(w.theta)
+    d = dev(case.data)
+    with pytest.raises(N.GnaError):
+        plan.eval_cached(d, dev(w.eta), w.sigma_eta)  # nothing kept yet
+    kw = dict(grad=True, grad_eta=True, mu=True, spectra=True)
+    plan.eval(p, d, dev(w.eta), w.sigma_eta, **kw)
+    rng = np.random.default_rng(8)
+    eta2 = dev(rng.normal(0.0, 0.02, w.nbins))
+    d2 = dev(rng.poisson(case.data).astype(np.float64))
+    for eta_c, d_c in ((eta2, d), (eta2, d2), (dev(w.eta), d2)):
+        c = {k: v.clone() for k, v in plan.eval_cached(d_c, eta_c, w.sigma_eta, **kw).items()}
+        f = plan.eval(p, d_c, eta_c, w.sigma_eta, **kw)
+        for k in c:
+            assert torch.equal(c[k], f[k]), (mapping, k)
+    # against the oracle too, for the last pair
+    ref = oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], case.N, d2.cpu().numpy(), w.kind, eta=w.eta,
+                       sigma=w.sigma_eta)
+    assert abs(c["chi2"][0].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, d2.cpu().numpy(), w.kind)
+    assert rel(c["mu"][0].cpu().numpy(), ref["mu"]) < 1e-6
+    # kept without a gradient: a gradient is refused, chi^2 alone is fine
+    plan.eval(p, d, grad=False)
+    with pytest.raises(N.GnaError):
+        plan.eval_cached(d, grad=True)
+    plan.eval_cached(d, grad=False)
+    plan.close()
+
+
 def test_autotune_keeps_parity(api):
     case = get_case("reactor8_40x3000")
     w = case.w

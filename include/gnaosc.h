@@ -307,15 +307,13 @@ int gna_plan_kernel_launches(const gna_plan* plan);
 
 /* gna_plan_profile: with on != 0, every evaluation outside graph capture
  * records a pair of CUDA events on its stream around the fused node kernel
- * (up to 8192 pairs).  gna_plan_profile_read synchronises those events and
+ * (with the slice mapping: the node kernel and the slice reduction; up to
+ * 8192 pairs).  gna_plan_profile_read synchronises those events and
  * returns the summed kernel time in ms and the number of timed launches,
  * then clears them. */
 gna_status gna_plan_profile(gna_plan* plan, int on);
 gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches);
 
-/* gna_plan_set_wait_limit: iteration limit of bounded device-side waits
- * (for tests; 0 restores the default). */
-gna_status gna_plan_set_wait_limit(gna_plan* plan, int64_t limit);
 
 /* ---------------------------------------------------------------------------
  * gna_chain_eval_noalloc: chi^2 (and optionally its gradient and the binned

@@ -87,7 +87,6 @@ SIGNATURES = {
     "gna_plan_set_tuning": (c_int, [c_void_p, c_char_p]),
     "gna_plan_set_graph": (c_int, [c_void_p, c_int]),
     "gna_plan_kernel_launches": (c_int, [c_void_p]),
-    "gna_plan_set_wait_limit": (c_int, [c_void_p, c_int64]),
     "gna_plan_profile": (c_int, [c_void_p, c_int]),
     "gna_plan_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "gna_chain_eval_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, ctypes.POINTER(c_double), c_int,

@@ -199,9 +199,6 @@ class Plan:
         self._check(self._lib.gna_plan_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)), "profile_read")
         return ms.value, n.value
 
-    def set_wait_limit(self, limit: int):
-        self._check(self._lib.gna_plan_set_wait_limit(self._h, int(limit)), "set_wait_limit")
-
     # ------------------------------------------------------- evaluation --
     def params_tensor(self, theta) -> torch.Tensor:
         t = torch.as_tensor(np.asarray(theta, dtype=np.float64).reshape(-1, 4), device=self.device)

@@ -147,7 +147,6 @@ struct gna_plan {
     int last_launches = 0;
     int64_t dev_bytes = 0;
     int* d_status = nullptr;
-    int64_t wait_limit = 0;
     std::vector<void*> allocs;
     // kernel timing
     bool profile = false;
@@ -1291,12 +1290,6 @@ gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches
     *total_ms = tot;
     *launches = plan->prof_n;
     plan->prof_n = 0;
-    return GNA_OK;
-}
-
-gna_status gna_plan_set_wait_limit(gna_plan* plan, int64_t limit) {
-    if (!plan || limit < 0) return GNA_EINVAL;
-    plan->wait_limit = limit;
     return GNA_OK;
 }
 

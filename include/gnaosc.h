@@ -24,8 +24,9 @@
  *     device, owned by the caller; "host" pointers are ordinary host memory.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls that take a stream only enqueue work on it and return;
- *     argument errors are returned at once, device-side failures (including
- *     bounded-wait timeouts) are reported by gna_plan_status().
+ *     argument errors are returned at once, device-side failures (CUDA
+ *     errors, parameter points outside the physical domain) are reported by
+ *     gna_plan_status().
  *   - Evaluation calls use only the memory gna_plan_create() allocated;
  *     the one call that allocates outside a plan is gna_gl_nodes (a
  *     temporary of 16 n bytes, freed before it returns).
@@ -48,7 +49,7 @@ typedef enum {
     GNA_ESHAPE = 2,   /* sizes inconsistent with the plan or out of range */
     GNA_ENOMEM = 3,   /* device or pinned-host allocation failed (plan creation only) */
     GNA_ECUDA = 4,    /* a CUDA runtime call failed */
-    GNA_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    GNA_ETIMEOUT = 5, /* reserved: no call waits on a device flag */
     GNA_ESTATE = 6    /* call not valid in the plan's current state */
 } gna_status;
 
@@ -181,8 +182,12 @@ gna_status gna_plan_destroy(gna_plan* plan);
 const char* gna_plan_error(const gna_plan* plan);
 
 /* gna_plan_status: synchronises the stream of the plan's last call and
- * returns the device status word (GNA_OK, GNA_ETIMEOUT, ...) or GNA_ECUDA
- * if an asynchronous CUDA error was raised.  Clears the status word. */
+ * returns GNA_ECUDA if an asynchronous CUDA error was raised, else the device
+ * status word: GNA_EINVAL when an evaluation met a parameter point outside
+ * the physical domain (s2 outside [0, 1], a mass splitting not finite; the
+ * parameters live on the device, so this is found there), else GNA_OK.
+ * Clears the status word.  (No kernel waits on a flag, so GNA_ETIMEOUT is
+ * never returned; the code is kept for the ABI.) */
 gna_status gna_plan_status(gna_plan* plan);
 
 /* gna_plan_info: sizes of the plan (host pointers; any may be NULL):

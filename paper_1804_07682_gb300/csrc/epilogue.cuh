@@ -1,4 +1,5 @@
-// epilogue.cuh -- steps a7-a9 inside the node kernels (last-arriver pattern).
+// epilogue.cuh -- steps a7-a9, run by the warps that finish the node sums
+// (last-arriver pattern), or by the slice reduction and the cached re-evaluation.
 //
 // Per (point, bin), once its node sums are complete:
 //   M_i = sum_r omega_r mu_r,i,  mu_i = N (1 + eta_i) M_i,
@@ -7,8 +8,8 @@
 // plus eta_i^2 / sigma^2, the gradient terms g_i N (1+eta_i) dM_i/dtheta,
 // d chi2 / d eta_i = g_i N M_i + 2 eta_i / sigma^2 and, for the fitter,
 // (2 / mu_i) J_i J_i^T with J_i = N (1+eta_i) dM_i/dtheta.
-// The last bin of a point to finish sums the per-bin values over bins in a
-// fixed order (deterministic) and writes chi2, the gradient and J^T W J.
+// The per-bin values are then summed per group of 32 bins and per point, each
+// in a fixed order (deterministic), and chi2, the gradient and J^T W J written.
 //
 // In the mixed modes only mu_i and d_i - mu_i are formed in double (FP64
 // instructions are 1/64 of the FP32 rate on this part); t_i = (d_i - mu_i) /

@@ -379,7 +379,7 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     // kernel that prepares the per-point constants
     const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups) +
                          (plan->mapping == MAP_SPLIT ? (int64_t)plan->npts * plan->nbins : 0);
-    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s, plan->d_counters, ncnt));
+    CU(launch_prepare(q.params, plan->npts, plan->bc, plan->d_pc, s, plan->d_counters, ncnt, plan->d_status));
     nl++;
     EpiArgs ea = make_epi(plan, q, grad, spec, NV);
     // keep the node sums for epilogue-only re-evaluations (not in fits)
@@ -1070,7 +1070,7 @@ gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const dou
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     const bool grad = out->grad || out->grad_eta;
-    CU(launch_prepare(params, plan->npts, plan->bc, plan->d_pc, s));
+    CU(launch_prepare(params, plan->npts, plan->bc, plan->d_pc, s, nullptr, 0, plan->d_status));
     int nl = 1;
     for (int p = 0; p < plan->npts; p++) {
         PlainChi2Args ca{};

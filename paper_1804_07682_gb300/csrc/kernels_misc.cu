@@ -22,7 +22,7 @@ namespace gna {
 // programmatic dependent: it may be launched as soon as this kernel starts and
 // waits in hardware for its completion before touching counters or constants).
 __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, BaseConst bc, PointConst* __restrict__ out,
-                                 int* __restrict__ zero, int64_t nz) {
+                                 int* __restrict__ zero, int64_t nz, int* __restrict__ status) {
     asm volatile("griddepcontrol.launch_dependents;");
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t k = tid; k < nz; k += (int64_t)gridDim.x * blockDim.x) zero[k] = 0;
@@ -31,6 +31,13 @@ __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, Base
     if (p >= npts) return;
     const gna_osc o = prm[p];
     PointConst& pc = out[p];
+    // the parameters live on the device: a point outside the physical domain
+    // (s2 outside [0, 1], a mass splitting not finite) is reported through the
+    // plan's status word (gna_plan_status); its results are not meaningful
+    if (r == 0 && status &&
+        !(o.s2_12 >= 0.0 && o.s2_12 <= 1.0 && o.s2_13 >= 0.0 && o.s2_13 <= 1.0 && isfinite(o.dm2_21) &&
+          isfinite(o.dm2_32)))
+        atomicExch(status, (int)GNA_EINVAL);
     const double kl = (r < bc.nL) ? bc.kld[r] : 0.0;
     const double c21 = o.dm2_21 * kl, c32 = o.dm2_32 * kl;
     pc.c21[r] = c21;
@@ -63,9 +70,9 @@ __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, Base
 }
 
 cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s,
-                           int* zero, int64_t nz) {
+                           int* zero, int64_t nz, int* status) {
     const int64_t threads = std::max<int64_t>((int64_t)npts * GNA_NLMAX, std::min<int64_t>(nz, 1LL << 20));
-    k_prepare_points<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, out, zero, nz);
+    k_prepare_points<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, out, zero, nz, status);
     return cudaGetLastError();
 }
 

@@ -56,9 +56,10 @@ struct LMState {
     double lam;
 };
 
-// Per-point constants (step a0); also zeroes nz ints at zero (the evaluation's counters).
+// Per-point constants (step a0); also zeroes nz ints at zero (the evaluation's
+// counters) and sets *status to GNA_EINVAL for a point outside the physical domain.
 cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s,
-                           int* zero = nullptr, int64_t nz = 0);
+                           int* zero = nullptr, int64_t nz = 0, int* status = nullptr);
 cudaError_t launch_gl(int n, double* x, double* w, double* tmp_ab, cudaStream_t s);
 cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int n, const double* x, const double* w,
                               double e_scale, int layout, float4* ff, double2* d64, double2* plain64, cudaStream_t s);

@@ -445,6 +445,24 @@ def test_fits_match_oracle(api, prec):
         assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
 
 
+def test_device_status_flags_unphysical_points(api):
+    # the parameters live on the device; a point with s2 > 1 is found there
+    # and reported by status(), which then clears
+    from paper_1804_07682_gb300 import _native as N
+    case = get_case("reactor_200x50")
+    w = case.w
+    plan = make_plan(api, case, "ff")
+    d = dev(case.data)
+    bad = np.array(w.theta, dtype=np.float64).reshape(1, 4).copy()
+    bad[0, 0] = 1.5
+    plan.eval(plan.params_tensor(bad), d, grad=True)
+    with pytest.raises(N.GnaError):
+        plan.status()
+    plan.eval(plan.params_tensor(w.theta), d, grad=True)
+    plan.status()
+    plan.close()
+
+
 def test_bad_arguments_raise(api):
     from paper_1804_07682_gb300 import _native as N
 

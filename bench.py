@@ -373,6 +373,20 @@ def side_workloads(api, torch, device, args):
             ms = a0.elapsed_time(a1) / reps
             gen["%s->%s %s" % (a, b, prec)] = {"us": ms * 1e3, "gpoints_per_s": 1e6 / (ms * 1e-3) / 1e9}
     out["oscprob_any_channel_810km_1e6"] = gen
+    # the fits workload's 16384 x 1000 Poisson pseudo-data drawn on the device
+    wf = wl.fits_16384x1000()
+    mu_f = np.linspace(20.0, 400.0, wf.nbins)
+    api.poisson_datasets(mu_f, 16, 4)
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    for _ in range(5):
+        api.poisson_datasets(mu_f, wf.npts, 4)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / 5
+    out["pseudo_data_16384x1000"] = {"ms": ms, "gsamples_per_s": wf.npts * wf.nbins / (ms * 1e-3) / 1e9,
+                                     "mu_range": [20.0, 400.0]}
     return out
 
 

@@ -126,6 +126,25 @@ const char* gna_strerror(gna_status s);
 gna_status gna_gl_nodes(int n, double* x, double* w, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * gna_poisson_datasets: Poisson pseudo-data for batched fits (the
+ * pseudo-experiments of the fits workload; not a step of the paper's chain),
+ * generated on the device: data_out[j][i] ~ Poisson(mu[i]) for data sets
+ * j < ndatasets.  Counter-based and reproducible: a mean is drawn as the sum
+ * of M = ceil(mu / 500) parts of mean m = mu / M; part q of bin i in data set
+ * j uses Philox4x32-10 (Salmon et al., SC'11) of the counter (i, j mod 2^32,
+ * j / 2^32, q) under the key (seed mod 2^32, seed / 2^32), one 53-bit
+ * uniform u = ((x0 >> 5) 2^26 + (x1 >> 6)) 2^-53, and inversion: the
+ * smallest k with F(k) >= u, p_0 = e^-m (computed on the host), p_k =
+ * p_{k-1} m / k, at most 10 m + 100 steps, each operation rounded once.
+ * Draws do not depend on the launch shape; the cost is O(mu) per sample.
+ *   mu:       host [nbins], each in [0, 1e7] (GNA_EINVAL otherwise)
+ *   data_out: device [ndatasets][nbins] double (integer values)
+ * Uses a stream-ordered temporary of 2 nbins doubles and nbins ints.
+ */
+gna_status gna_poisson_datasets(const double* mu, int nbins, int64_t ndatasets, uint64_t seed, double* data_out,
+                                void* stream);
+
+/* ---------------------------------------------------------------------------
  * gna_oscprob_ee: element-wise OscProb transformation, paper Sec. 4.1
  * (P(nue_bar -> nue_bar), i.e. alpha = beta = e of the general formula, for
  * which the Im term vanishes): P[r][k] = 1 - sum_{i>j} A_ij sin^2(phase_ij)

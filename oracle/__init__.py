@@ -11,7 +11,9 @@ differences and the Levenberg-Marquardt fit loop.
 
 Parity status of every function is pinned by ``tests/test_oracle_pins.py``
 (closed forms, amplitude brute force, library quadrature, erf integrals,
-finite differences); nothing here is "parity unpinned".
+finite differences) and ``tests/test_oracle_pseudo.py`` (the generator's
+known-answer vectors, the inversion's boundaries, the exact Poisson law);
+nothing here is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -38,7 +40,8 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (gcc, -O2, OpenMP when available)."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
-    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fno-fast-math", _SRC,
+            "-o", _LIB_PATH + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -63,6 +66,11 @@ def _configure(lib):
     lib.or_binned.restype = _I
     lib.or_chi2.argtypes = [_I, _I, _PD, _PD, _PD, _D, _PD, _D, _PD, _I, _PD, _PD, _PD]
     lib.or_chi2.restype = _D
+    _PU = ctypes.POINTER(ctypes.c_uint32)
+    lib.or_philox4x32_10.argtypes = [_PU, _PU, _PU]
+    lib.or_poisson_inv.argtypes = [_D, _D, _D]
+    lib.or_poisson_inv.restype = _I64
+    lib.or_pseudo_data.argtypes = [_PD, _PD, ctypes.POINTER(ctypes.c_int), _I, _I64, _I64, ctypes.c_uint64, _PD]
     return lib
 
 
@@ -281,3 +289,35 @@ def fit_lm(evaluate, theta0, iters=20, lam0=1e-3, lo=(1e-6, 1e-6, 1e-7, 1e-7), h
         delta = np.linalg.solve(A, -g)
         trial = np.minimum(np.maximum(best_theta + delta, lo), hi)
     return best_theta, best_chi2, np.array(hist)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one 4 x 32-bit counter under a 2 x 32-bit key."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.empty(4, dtype=np.uint32)
+    PU = ctypes.POINTER(ctypes.c_uint32)
+    _load().or_philox4x32_10(c.ctypes.data_as(PU), k.ctypes.data_as(PU), out.ctypes.data_as(PU))
+    return out
+
+
+def poisson_inv(mu: float, u: float) -> int:
+    """Poisson(mu) by inversion of one uniform (e^-mu from the host's libm)."""
+    import math
+
+    return int(_load().or_poisson_inv(float(mu), math.exp(-float(mu)), float(u)))
+
+
+def pseudo_data(mu, nds: int, seed: int, j0: int = 0) -> np.ndarray:
+    """Poisson pseudo-data sets j0 .. j0 + nds - 1 of the bin means mu: [nds][nbins].
+    A mean is drawn as the sum of M = ceil(mu / 500) parts of mean mu / M."""
+    import math
+
+    m = _f64(mu)
+    parts = np.array([max(1, math.ceil(v / 500.0)) for v in m], dtype=np.int32)
+    mp = np.array([v / int(c) for v, c in zip(m, parts)])
+    em = np.array([math.exp(-v) for v in mp])  # the C library's exp, as the product's host code uses
+    out = np.empty((int(nds), m.size))
+    _load().or_pseudo_data(_p(mp), _p(em), parts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), m.size, int(j0),
+                           int(nds), ctypes.c_uint64(int(seed)), _p(out))
+    return out

@@ -330,3 +330,71 @@ double or_chi2(int nbins, int nL, const double* omega, const double* mu_rb,
     }
     return chi2;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Pseudo-data (beyond the paper: the pseudo-experiments of the batched     */
+/* fits).  Philox4x32-10, the counter-based generator of Salmon, Moraes,    */
+/* Dror and Shaw (SC'11), from its published definition: ten rounds of      */
+/*   (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2 (32 x 32 -> 64 bits),       */
+/*   c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0),                          */
+/* with the key bumped by (W0, W1) before every round but the first.        */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    for (int i = 0; i < 4; i++) out[i] = c[i];
+}
+
+/* Poisson(mu) by inversion from one uniform u in [0, 1): the smallest k   */
+/* with F(k) = sum_{j<=k} p_j >= u, p_0 = e^-mu (given: em), p_j =          */
+/* p_{j-1} mu / j; at most kmax = 10 mu + 100 steps.  Only +, *, / in      */
+/* double, each rounded once (no contraction), so that another             */
+/* implementation with the same operations draws the same integers.       */
+int64_t or_poisson_inv(double mu, double em, double u) {
+    const int64_t kmax = (int64_t)(10.0 * mu) + 100;
+    int64_t k = 0;
+    double p = em, F = em;
+    while (u > F && k < kmax) {
+        k++;
+        p = (p * mu) / (double)k;
+        F = F + p;
+    }
+    return k;
+}
+
+/* Data set j, bin i: the sum of M_i parts, part m ~ Poisson(mu_i / M_i)   */
+/* from the counter (i, j_lo, j_hi, m) under the key (seed_lo, seed_hi)     */
+/* (M_i = ceil(mu_i / 500), so that e^-(mu_i / M_i) stays a normal number); */
+/* u = ((x0 >> 5) 2^26 + (x1 >> 6)) 2^-53 from the first two outputs.       */
+/* mu_part, em_part and parts are formed by the caller.                     */
+void or_pseudo_data(const double* mu_part, const double* em_part, const int* parts, int nbins, int64_t j0,
+                    int64_t nds, uint64_t seed, double* out) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t j = j0; j < j0 + nds; j++)
+        for (int i = 0; i < nbins; i++) {
+            int64_t k = 0;
+            for (int m = 0; m < parts[i]; m++) {
+                const uint32_t ctr[4] = {(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), (uint32_t)m};
+                uint32_t x[4];
+                or_philox4x32_10(ctr, key, x);
+                const double u = ((double)(x[0] >> 5) * 67108864.0 + (double)(x[1] >> 6)) * (1.0 / 9007199254740992.0);
+                k += or_poisson_inv(mu_part[i], em_part[i], u);
+            }
+            out[(j - j0) * nbins + i] = (double)k;
+        }
+}

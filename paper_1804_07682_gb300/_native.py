@@ -63,6 +63,7 @@ SIGNATURES = {
     "gna_pmns": (c_int, [ctypes.POINTER(GnaOscFull), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "gna_oscprob": (c_int, [c_void_p, c_int64, ctypes.POINTER(c_double), c_int, c_int, c_int, c_int,
                             ctypes.POINTER(GnaOscFull), c_int, c_void_p, c_void_p]),
+    "gna_poisson_datasets": (c_int, [ctypes.POINTER(c_double), c_int, c_int64, ctypes.c_uint64, c_void_p, c_void_p]),
     "gna_oscprob_ee": (c_int, [c_void_p, c_int64, ctypes.POINTER(c_double), c_int, ctypes.POINTER(GnaOsc), c_int,
                                c_void_p, c_void_p]),
     "gna_plan_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(GnaPlanDesc), c_void_p]),

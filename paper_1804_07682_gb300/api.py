@@ -100,6 +100,18 @@ def oscprob_general(E: torch.Tensor, L: Sequence[float], theta_full: Sequence[fl
     return P
 
 
+def poisson_datasets(mu, ndatasets: int, seed: int, stream=None) -> torch.Tensor:
+    """Poisson pseudo-data [ndatasets, nbins] (float64, CUDA) of the bin means mu
+    (host, each in [0, 700]), reproducible from the seed (counter-based)."""
+    _require_cuda()
+    m = _f64(mu)
+    out = torch.empty((int(ndatasets), m.size), dtype=torch.float64, device="cuda")
+    code = N.lib().gna_poisson_datasets(m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), m.size, int(ndatasets),
+                                        ctypes.c_uint64(int(seed)), _ptr(out), ctypes.c_void_p(_stream(stream)))
+    N.check(code, what="gna_poisson_datasets")
+    return out
+
+
 class Plan:
     """A configured chain (paper's configuration stage): energy grids built and
     all scratch allocated on the device; evaluations only launch kernels."""

@@ -114,3 +114,17 @@ def _cached(key, fn):
     if key not in _cache:
         _cache[key] = fn()
     return _cache[key]
+
+
+def test_pseudo_data_full_size_sampled(api):
+    # the 16384 x 1000 pseudo-experiments of the fits workload drawn on the
+    # device; sampled data sets (first, middle, last) against the oracle
+    w = wl.fits_16384x1000()
+    case = _cached("fits_case", lambda: Case(w))
+    d = api.poisson_datasets(case.mu_truth, w.npts, 4)
+    assert tuple(d.shape) == (w.npts, w.nbins)
+    for j in (0, 8191, 16383):
+        ref = oracle.pseudo_data(case.mu_truth, 1, 4, j0=j)[0]
+        assert np.array_equal(d[j].cpu().numpy(), ref), j
+    m = d.mean(0).cpu().numpy()
+    assert np.abs(m - case.mu_truth).max() < 6 * np.sqrt(case.mu_truth.max() / w.npts) + 1e-9

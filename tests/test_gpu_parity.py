@@ -445,6 +445,22 @@ def test_fits_match_oracle(api, prec):
         assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
 
 
+def test_pseudo_data_matches_oracle_bit_for_bit(api):
+    # counter-based draws: the device and the oracle give the same integers
+    case = get_case("fits_8x100x20")
+    mu = np.concatenate([case.mu_truth, [0.0, 1e-3, 0.7, 699.0, 500.0, 500.001, 12345.6]])
+    for seed in (4, 2 ** 40 + 17):
+        dev_data = api.poisson_datasets(mu, 300, seed).cpu().numpy()
+        ref = oracle.pseudo_data(mu, 300, seed)
+        assert np.array_equal(dev_data, ref), seed
+    # a prefix does not depend on how many sets one launch draws
+    assert np.array_equal(api.poisson_datasets(mu, 40, 4).cpu().numpy(), oracle.pseudo_data(mu, 40, 4))
+    from paper_1804_07682_gb300 import _native as N
+    with pytest.raises(N.GnaError):
+        api.poisson_datasets([1.0, 2e7], 2, 1)
+    assert api.poisson_datasets([1.0], 0, 1).numel() == 0
+
+
 def test_device_status_flags_unphysical_points(api):
     # the parameters live on the device; a point with s2 > 1 is found there
     # and reported by status(), which then clears

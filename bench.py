@@ -62,8 +62,8 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
 TRAFFIC_CAPTURE = {
     "split": {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
               "bytes": 265113600 + 4114176},
-    "slices": {"sources_sha256": "b46c944c4bc17ec50e2ee604fb72594d4a5daec0ba2ab247bf9b300c13683f2f",
-               "bytes": 268521472 + 4717056 + 8175360},
+    "slices": {"sources_sha256": "2c38c9bd88d1844ab9261339b3f69e62c02dffd7e8abbd2ee6da78c02cc33a8d",
+               "bytes": 268521984 + 4973056 + 8176128},
 }
 KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
                   "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h",
@@ -351,7 +351,28 @@ def side_workloads(api, torch, device, args):
             P_h.copy_(P, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         gpu_xfer_ms = (time.perf_counter() - t0) * 1e3 / reps
-        t1[str(n)] = {"gpu_compute_ms": gpu_ms, "gpu_with_transfer_ms": gpu_xfer_ms}
+        def host_ms(fn):
+            for _ in range(5):
+                fn()
+            torch.cuda.current_stream().synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+                torch.cuda.current_stream().synchronize()
+            return (time.perf_counter() - t0) * 1e3 / reps
+
+        # host to host without copies (the kernel reads E and writes P in
+        # pinned host memory over the host link), and through device staging
+        # in chunks whose transfers overlap the evaluation
+        row = {"gpu_compute_ms": gpu_ms, "gpu_with_transfer_ms": gpu_xfer_ms}
+        for prec in ("fp64", "ff"):
+            P_pin = torch.empty(1, n, dtype=torch.float64 if prec == "fp64" else torch.float32).pin_memory()
+            key = "" if prec == "fp64" else "_ff"
+            row["gpu_host_memory_in_place_ms" + key] = host_ms(
+                lambda: api.oscprob(E_h, [52.5], wl.TRUTH, prec, out=P_pin))
+            row["gpu_staged_chunks_ms" + key] = host_ms(
+                lambda: api.oscprob_staged(E_h, [52.5], wl.TRUTH, prec, out=P_pin))
+        t1[str(n)] = row
     out["oscprob_fp64_table1_shape"] = t1
     # any channel (general formula with the CP term): numu -> nue and numu ->
     # numu at 810 km on 10^6 energies in 0.5-5 GeV, FP64 and mixed
@@ -406,6 +427,8 @@ def cpu_oscprob_table1(t1):
         cpu_ms = (time.perf_counter() - t0) * 1e3 / 5
         row.update({"cpu_oracle_ms": cpu_ms, "cpu_threads": oracle.threads(),
                     "cpu_over_gpu_with_transfer": cpu_ms / row["gpu_with_transfer_ms"],
+                    "cpu_over_gpu_host_memory_in_place": cpu_ms / row["gpu_host_memory_in_place_ms"],
+                    "cpu_over_gpu_staged_chunks": cpu_ms / row["gpu_staged_chunks_ms"],
                     "cpu_over_gpu_compute": cpu_ms / row["gpu_compute_ms"]})
 
 

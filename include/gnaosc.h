@@ -149,16 +149,43 @@ gna_status gna_poisson_datasets(const double* mu, int nbins, int64_t ndatasets, 
  * (P(nue_bar -> nue_bar), i.e. alpha = beta = e of the general formula, for
  * which the Im term vanishes): P[r][k] = 1 - sum_{i>j} A_ij sin^2(phase_ij)
  * at E[k], L[r].
- *   E:     device [n] double, MeV, > 0
+ *   E:     device [n] double, MeV, > 0 -- or pinned host memory: the kernel
+ *          reads it in place over the host link (unified addressing), so a
+ *          host-to-host evaluation needs no staging copies
  *   L:     host [nL] double, km; nL in 1..16
  *   p:     host, one parameter point
  *   prec:  GNA_FP64 writes double P; the mixed modes write float P
- *   P_out: device [nL][n] of double (GNA_FP64) or float (mixed)
+ *   P_out: device (or pinned host) [nL][n] of double (GNA_FP64) or float (mixed)
  * n = 0 is valid and launches nothing.  Returns GNA_EINVAL for NULL
- * pointers or an unknown precision, GNA_ESHAPE for n < 0 or bad nL.
+ * pointers, for E or P_out that the device cannot address (host memory that
+ * is neither page-locked nor coherently accessible), or an unknown
+ * precision; GNA_ESHAPE for n < 0 or bad nL.
  */
 gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p,
                           gna_precision prec, void* P_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gna_oscprob_ee_staged: gna_oscprob_ee from host memory to host memory
+ * through device staging buffers, in chunks whose transfers overlap the
+ * evaluation (paper Sec. 4.2: CUDA streams, data in chunks, asynchronous
+ * copies).  Chunk c goes to stage c mod 3, each stage an internal stream:
+ * upload of E[chunk], evaluation, download of the nL rows of P[chunk]; so the
+ * upload of one chunk, the evaluation of the next and the download of the one
+ * before run at the same time.
+ *   E_host: page-locked host [n] double, MeV, > 0
+ *   P_host: page-locked host [nL][n] of double (GNA_FP64) or float (mixed)
+ *   chunk:  energies per chunk; 0 = max(65536, ceil(n / 8))
+ *   L, nL, p, prec: as for gna_oscprob_ee
+ * Asynchronous: the stages start after the work queued on `stream` and
+ * `stream` waits for all of them, so P_host is complete once `stream` has
+ * synchronised.  Staging memory comes from the stream-ordered allocator and
+ * goes back to it on `stream`.  The result equals gna_oscprob_ee's bit for
+ * bit.  GNA_EINVAL for NULL pointers, host memory that is not page-locked
+ * (device memory included) or an unknown precision; GNA_ESHAPE for n < 0,
+ * chunk < 0 or bad nL; GNA_ECUDA if a copy or launch could not be queued.
+ */
+gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* L, int nL, const gna_osc* p,
+                                 gna_precision prec, void* P_host, int64_t chunk, void* stream);
 
 /* ---------------------------------------------------------------------------
  * gna_pmns: the mixing matrix U[alpha][i] (alpha = e, mu, tau; i = 1, 2, 3)

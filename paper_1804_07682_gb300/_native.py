@@ -66,6 +66,8 @@ SIGNATURES = {
     "gna_poisson_datasets": (c_int, [ctypes.POINTER(c_double), c_int, c_int64, ctypes.c_uint64, c_void_p, c_void_p]),
     "gna_oscprob_ee": (c_int, [c_void_p, c_int64, ctypes.POINTER(c_double), c_int, ctypes.POINTER(GnaOsc), c_int,
                                c_void_p, c_void_p]),
+    "gna_oscprob_ee_staged": (c_int, [c_void_p, c_int64, ctypes.POINTER(c_double), c_int, ctypes.POINTER(GnaOsc),
+                                      c_int, c_void_p, c_int64, c_void_p]),
     "gna_plan_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(GnaPlanDesc), c_void_p]),
     "gna_plan_destroy": (c_int, [c_void_p]),
     "gna_plan_error": (c_char_p, [c_void_p]),

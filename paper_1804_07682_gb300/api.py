@@ -23,6 +23,16 @@ def _stream(stream=None) -> int:
     return s.cuda_stream
 
 
+def _ptr_any(t: torch.Tensor):
+    """Pointer to a CUDA tensor or to pinned host memory (mapped into the device's
+    address space: kernels read and write it in place)."""
+    if not (t.is_cuda or t.is_pinned()):
+        raise ValueError("expected a CUDA tensor or pinned host memory")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _ptr(t: Optional[torch.Tensor]):
     if t is None:
         return None
@@ -52,18 +62,61 @@ def gl_nodes(n: int, device="cuda"):
     return x, w
 
 
-def oscprob(E: torch.Tensor, L: Sequence[float], theta: Sequence[float], prec: str = "fp64") -> torch.Tensor:
-    """Element-wise OscProb: P(nue_bar -> nue_bar) [nL, n] at energies E (MeV) for baselines L (km)."""
+def _oscprob_out(E: torch.Tensor, nL: int, prec: str, out: Optional[torch.Tensor]) -> torch.Tensor:
+    """Output of the element-wise calls: on E's device, or, for E in pinned host
+    memory (read by the kernel in place over the host link), in pinned host memory."""
+    out_dtype = torch.float64 if prec == "fp64" else torch.float32
+    if out is not None:
+        if out.dtype != out_dtype or tuple(out.shape) != (nL, E.numel()):
+            raise ValueError("out must be %s [%d, %d]" % (out_dtype, nL, E.numel()))
+        if not out.is_cuda and not out.is_pinned():
+            raise ValueError("a host output must be pinned")
+        return out
+    if E.is_cuda:
+        return torch.empty((nL, E.numel()), dtype=out_dtype, device=E.device)
+    if not E.is_pinned():
+        raise ValueError("E must be a CUDA tensor or pinned host memory")
+    return torch.empty((nL, E.numel()), dtype=out_dtype).pin_memory()
+
+
+def oscprob(E: torch.Tensor, L: Sequence[float], theta: Sequence[float], prec: str = "fp64",
+            out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Element-wise OscProb: P(nue_bar -> nue_bar) [nL, n] at energies E (MeV) for baselines L (km).
+    E and out may be CUDA tensors or pinned host memory (the kernel reads and writes it in place)."""
     _require_cuda()
     if E.dtype != torch.float64:
         raise ValueError("E must be float64")
+    if not E.is_cuda and not E.is_pinned():
+        raise ValueError("E must be a CUDA tensor or pinned host memory")
     Ls = _f64(L)
     p = N.GnaOsc(*[float(t) for t in theta])
-    out_dtype = torch.float64 if prec == "fp64" else torch.float32
-    P = torch.empty((Ls.size, E.numel()), dtype=out_dtype, device=E.device)
-    code = N.lib().gna_oscprob_ee(_ptr(E.contiguous()), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                  Ls.size, ctypes.byref(p), PRECISIONS[prec], _ptr(P), ctypes.c_void_p(_stream()))
+    P = _oscprob_out(E, Ls.size, prec, out)
+    code = N.lib().gna_oscprob_ee(_ptr_any(E), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  Ls.size, ctypes.byref(p), PRECISIONS[prec], _ptr_any(P), ctypes.c_void_p(_stream()))
     N.check(code, what="gna_oscprob_ee")
+    return P
+
+
+def oscprob_staged(E: torch.Tensor, L: Sequence[float], theta: Sequence[float], prec: str = "fp64",
+                   out: Optional[torch.Tensor] = None, chunk: int = 0) -> torch.Tensor:
+    """OscProb from pinned host E to pinned host P [nL, n] through device staging
+    buffers, chunk by chunk, with the transfers overlapping the evaluation
+    (gna_oscprob_ee_staged).  Ordered on the current stream: P is complete once
+    that stream has synchronised."""
+    _require_cuda()
+    if E.dtype != torch.float64:
+        raise ValueError("E must be float64")
+    if E.is_cuda or not E.is_pinned():
+        raise ValueError("E must be pinned host memory")
+    Ls = _f64(L)
+    p = N.GnaOsc(*[float(t) for t in theta])
+    P = _oscprob_out(E, Ls.size, prec, out)
+    if P.is_cuda:
+        raise ValueError("out must be pinned host memory")
+    code = N.lib().gna_oscprob_ee_staged(_ptr_any(E), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         Ls.size, ctypes.byref(p), PRECISIONS[prec], _ptr_any(P), int(chunk),
+                                         ctypes.c_void_p(_stream()))
+    N.check(code, what="gna_oscprob_ee_staged")
     return P
 
 
@@ -81,20 +134,22 @@ def pmns(theta_full: Sequence[float]) -> np.ndarray:
 
 
 def oscprob_general(E: torch.Tensor, L: Sequence[float], theta_full: Sequence[float], alpha="mu", beta="e",
-                    anti: bool = False, prec: str = "fp64") -> torch.Tensor:
+                    anti: bool = False, prec: str = "fp64", out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Element-wise OscProb for any channel: P(alpha -> beta) [nL, n] at energies E (MeV) for
-    baselines L (km); theta_full = (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32)."""
+    baselines L (km); theta_full = (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32).  E and out
+    may be CUDA tensors or pinned host memory."""
     _require_cuda()
     if E.dtype != torch.float64:
         raise ValueError("E must be float64")
+    if not E.is_cuda and not E.is_pinned():
+        raise ValueError("E must be a CUDA tensor or pinned host memory")
     a = FLAVOURS.get(alpha, alpha)
     b = FLAVOURS.get(beta, beta)
     Ls = _f64(L)
     p = N.GnaOscFull(*[float(t) for t in theta_full])
-    out_dtype = torch.float64 if prec == "fp64" else torch.float32
-    P = torch.empty((Ls.size, E.numel()), dtype=out_dtype, device=E.device)
-    code = N.lib().gna_oscprob(_ptr(E.contiguous()), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                               Ls.size, int(a), int(b), int(bool(anti)), ctypes.byref(p), PRECISIONS[prec], _ptr(P),
+    P = _oscprob_out(E, Ls.size, prec, out)
+    code = N.lib().gna_oscprob(_ptr_any(E), E.numel(), Ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               Ls.size, int(a), int(b), int(bool(anti)), ctypes.byref(p), PRECISIONS[prec], _ptr_any(P),
                                ctypes.c_void_p(_stream()))
     N.check(code, what="gna_oscprob")
     return P

@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -495,14 +496,34 @@ gna_status gna_gl_nodes(int n, double* x, double* w, void* stream) {
     return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
 }
 
-gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p, gna_precision prec,
-                          void* P_out, void* stream) {
-    if (n < 0 || nL < 1 || nL > GNA_NLMAX) return GNA_ESHAPE;
-    if (!L || !p) return GNA_EINVAL;
-    if (prec != GNA_FP64 && prec != GNA_MIXED_F64PHASE && prec != GNA_MIXED_FFPHASE) return GNA_EINVAL;
-    if (n == 0) return GNA_OK;
-    if (!E || !P_out) return GNA_EINVAL;
-    OscConst oc{};
+// Whether a kernel on the current device may dereference ptr: device or managed
+// memory, page-locked host memory mapped at the same address (unified
+// addressing), or ordinary host memory where the device reports coherent access
+// to pageable memory.  Anything else is refused before a launch could fault.
+static bool device_accessible(const void* ptr) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    switch (at.type) {
+        case cudaMemoryTypeDevice:
+        case cudaMemoryTypeManaged: return true;
+        case cudaMemoryTypeHost: return at.devicePointer == ptr;
+        default: {
+            int dev = 0, pageable = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) return false;
+            if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return false;
+            return pageable != 0;
+        }
+    }
+}
+
+// Constants of the nue_bar survival probability for one parameter point and nL
+// baselines (Sec. 4.1 with alpha = beta = e): amplitudes A_ij and the phase
+// coefficients K dm2 L, also as float pairs for the double-float modes.
+static gna_status ee_constants(const double* L, int nL, const gna_osc* p, OscConst& oc) {
+    oc = OscConst{};
     oc.nL = nL;
     const double s12 = p->s2_12, s13 = p->s2_13;
     oc.A[0] = 4.0 * s12 * (1 - s12) * (1 - s13) * (1 - s13);
@@ -519,8 +540,115 @@ gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, c
         split_ff(oc.c32[r], oc.c32h[r], oc.c32l[r]);
         split_ff(oc.c21[r] + oc.c32[r], oc.c31h[r], oc.c31l[r]);
     }
+    return GNA_OK;
+}
+
+gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p, gna_precision prec,
+                          void* P_out, void* stream) {
+    if (n < 0 || nL < 1 || nL > GNA_NLMAX) return GNA_ESHAPE;
+    if (!L || !p) return GNA_EINVAL;
+    if (prec != GNA_FP64 && prec != GNA_MIXED_F64PHASE && prec != GNA_MIXED_FFPHASE) return GNA_EINVAL;
+    if (n == 0) return GNA_OK;
+    if (!E || !P_out) return GNA_EINVAL;
+    if (!device_accessible(E) || !device_accessible(P_out)) return GNA_EINVAL;
+    OscConst oc;
+    if (ee_constants(L, nL, p, oc) != GNA_OK) return GNA_EINVAL;
     cudaError_t e = launch_oscprob(E, n, oc, prec, P_out, (cudaStream_t)stream);
     return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
+}
+
+namespace {
+// Copy/compute streams of the staged transfer pipeline, created once per device.
+constexpr int kStages = 3;
+struct StageStreams {
+    cudaStream_t s[kStages];
+};
+std::mutex g_stage_mu;
+std::map<int, StageStreams> g_stage_streams;
+
+cudaError_t stage_streams(StageStreams& out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    auto it = g_stage_streams.find(dev);
+    if (it == g_stage_streams.end()) {
+        StageStreams ss{};
+        for (int j = 0; j < kStages; j++) {
+            e = cudaStreamCreateWithFlags(&ss.s[j], cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                for (int i = 0; i < j; i++) cudaStreamDestroy(ss.s[i]);
+                return e;
+            }
+        }
+        it = g_stage_streams.emplace(dev, ss).first;
+    }
+    out = it->second;
+    return cudaSuccess;
+}
+}  // namespace
+
+gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* L, int nL, const gna_osc* p,
+                                 gna_precision prec, void* P_host, int64_t chunk, void* stream) {
+    if (n < 0 || nL < 1 || nL > GNA_NLMAX || chunk < 0) return GNA_ESHAPE;
+    if (!L || !p) return GNA_EINVAL;
+    if (prec != GNA_FP64 && prec != GNA_MIXED_F64PHASE && prec != GNA_MIXED_FFPHASE) return GNA_EINVAL;
+    if (n == 0) return GNA_OK;
+    if (!E_host || !P_host) return GNA_EINVAL;
+    for (const void* q : {(const void*)E_host, (const void*)P_host}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+            cudaGetLastError();
+            return GNA_EINVAL;
+        }
+        if (at.type != cudaMemoryTypeHost) return GNA_EINVAL;  // page-locked host memory only
+    }
+    OscConst oc;
+    if (ee_constants(L, nL, p, oc) != GNA_OK) return GNA_EINVAL;
+    if (chunk == 0) chunk = std::max<int64_t>(int64_t(1) << 16, (n + 7) / 8);
+    chunk = std::min(chunk, n);
+    const size_t esz = prec == GNA_FP64 ? sizeof(double) : sizeof(float);
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    const int nslots = (int)std::min<int64_t>(kStages, nchunks);
+    const size_t e_bytes = size_t(chunk) * sizeof(double), p_bytes = size_t(chunk) * nL * esz;
+    StageStreams ss;
+    if (stage_streams(ss) != cudaSuccess) return GNA_ECUDA;
+    cudaStream_t cs = (cudaStream_t)stream;
+    char* buf = nullptr;
+    cudaEvent_t fork = nullptr, join[kStages] = {};
+    cudaError_t e = cudaMallocAsync((void**)&buf, nslots * (e_bytes + p_bytes), cs);
+    if (e != cudaSuccess) return GNA_ECUDA;
+    bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventRecord(fork, cs) == cudaSuccess;
+    int forked = 0;
+    for (int j = 0; ok && j < nslots; j++) {
+        ok = cudaEventCreateWithFlags(&join[j], cudaEventDisableTiming) == cudaSuccess &&
+             cudaStreamWaitEvent(ss.s[j], fork, 0) == cudaSuccess;
+        if (ok) forked = j + 1;
+    }
+    // chunk c on stage c mod nslots: upload its energies, evaluate, download its
+    // nL probability rows; the stages overlap the upload of one chunk with the
+    // evaluation of the next and the download of the one before
+    for (int64_t c = 0; ok && c < nchunks; c++) {
+        const int j = (int)(c % nslots);
+        const int64_t k0 = c * chunk, len = std::min(chunk, n - k0);
+        double* dE = (double*)(buf + j * (e_bytes + p_bytes));
+        char* dP = (char*)dE + e_bytes;
+        ok = cudaMemcpyAsync(dE, E_host + k0, len * sizeof(double), cudaMemcpyHostToDevice, ss.s[j]) == cudaSuccess &&
+             launch_oscprob(dE, len, oc, prec, dP, ss.s[j]) == cudaSuccess &&
+             cudaMemcpy2DAsync((char*)P_host + k0 * esz, n * esz, dP, len * esz, len * esz, nL,
+                               cudaMemcpyDeviceToHost, ss.s[j]) == cudaSuccess;
+    }
+    // join the stages back into the caller's stream (also after a failed
+    // enqueue, so that the staging memory is released behind what was queued)
+    for (int j = 0; j < forked; j++)
+        if (cudaEventRecord(join[j], ss.s[j]) != cudaSuccess || cudaStreamWaitEvent(cs, join[j], 0) != cudaSuccess)
+            ok = false;
+    if (cudaFreeAsync(buf, cs) != cudaSuccess) ok = false;
+    if (fork) cudaEventDestroy(fork);
+    for (int j = 0; j < kStages; j++)
+        if (join[j]) cudaEventDestroy(join[j]);
+    return ok ? GNA_OK : GNA_ECUDA;
 }
 
 gna_status gna_pmns(const gna_osc_full* p, double* U_re, double* U_im) {
@@ -554,6 +682,7 @@ gna_status gna_oscprob(const double* E, int64_t n, const double* L, int nL, int 
     if (gna_pmns(p, ure, uim) != GNA_OK) return GNA_EINVAL;
     if (n == 0) return GNA_OK;
     if (!E || !P_out) return GNA_EINVAL;
+    if (!device_accessible(E) || !device_accessible(P_out)) return GNA_EINVAL;
     // V = U or U*; X_ij = V*_ai V_bi V_aj V*_bj for (i, j) = (2, 1), (3, 1), (3, 2)
     auto V = [&](int a, int i) {
         return std::complex<double>(ure[3 * a + i], anti ? -uim[3 * a + i] : uim[3 * a + i]);

@@ -7,12 +7,15 @@ is compared at the same tolerance scaled by max(chi2, sum_i |g_i| mu_i): the
 largest chi^2 change a relative change of every mu_i can cause (plain
 relative error whenever chi^2 dominates).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
 import oracle
+from paper_1804_07682_gb300 import _native as N
 from paper_1804_07682_gb300 import workloads as wl
 from refs import Case, chi2_err_bound, normrel, rel
 
@@ -68,6 +71,59 @@ def test_oscprob(api, prec, rng_case):
     for r, Lr in enumerate(L):
         ref = oracle.pee(E, Lr, theta)
         assert rel(P[r], ref) < (1e-10 if prec == "fp64" else TOL[prec]), (prec, Lr)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_oscprob_reads_and_writes_pinned_host_memory(api, prec):
+    # energies and probabilities in pinned host memory, used in place by the kernels
+    rng = np.random.default_rng(12)
+    E = rng.uniform(0.5, 15.0, 200003)
+    Eh = torch.as_tensor(E).pin_memory()
+    Ph = api.oscprob(Eh, [52.5, 1.0], wl.TRUTH, prec)
+    Pd = api.oscprob(dev(E), [52.5, 1.0], wl.TRUTH, prec)
+    torch.cuda.synchronize()
+    assert not Ph.is_cuda and Ph.is_pinned()
+    assert torch.equal(Ph, Pd.cpu())
+    th = (0.307, 0.0218, 0.545, 1.2 * np.pi, 7.53e-5, 2.44e-3)
+    Gh = api.oscprob_general(Eh, [810.0], th, "mu", "e", prec=prec)
+    Gd = api.oscprob_general(dev(E), [810.0], th, "mu", "e", prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(Gh, Gd.cpu())
+    with pytest.raises(ValueError):
+        api.oscprob(torch.as_tensor(E), [52.5], wl.TRUTH, prec)  # pageable host memory is refused
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+@pytest.mark.parametrize("n,chunk", [(200003, 0), (200003, 65536), (200003, 7), (1000, 4096), (1, 0), (70001, 70000)])
+def test_oscprob_staged_chunks(api, prec, n, chunk):
+    # host to host through device staging in chunks (ragged last chunk, chunk
+    # larger than n, more chunks than stages): identical to the device result
+    rng = np.random.default_rng(n + chunk)
+    E = rng.uniform(0.5, 15.0, n)
+    if chunk == 7:
+        E = E[:5000]
+    Eh = torch.as_tensor(E).pin_memory()
+    Ph = api.oscprob_staged(Eh, [52.5, 1.0, 0.0], wl.TRUTH, prec, chunk=chunk)
+    Pd = api.oscprob(dev(E), [52.5, 1.0, 0.0], wl.TRUTH, prec)
+    torch.cuda.current_stream().synchronize()
+    assert Ph.is_pinned() and torch.equal(Ph, Pd.cpu())
+
+
+def test_oscprob_staged_refuses_unpinned(api):
+    E = torch.linspace(1.0, 10.0, 100, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        api.oscprob_staged(E, [52.5], wl.TRUTH)
+    with pytest.raises(ValueError):
+        api.oscprob_staged(E.cuda(), [52.5], wl.TRUTH)
+    # the C ABI itself refuses device memory for the host arguments
+    Ed = E.cuda()
+    Pd = torch.empty(1, 100, dtype=torch.float64, device="cuda")
+    p = N.GnaOsc(*wl.TRUTH)
+    L = np.array([52.5])
+    code = N.lib().gna_oscprob_ee_staged(ctypes.c_void_p(Ed.data_ptr()), 100,
+                                         L.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, ctypes.byref(p),
+                                         0, ctypes.c_void_p(Pd.data_ptr()), 0, None)
+    assert code == 1  # GNA_EINVAL
 
 
 def test_oscprob_edge_cases(api):

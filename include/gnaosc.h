@@ -158,8 +158,8 @@ gna_status gna_poisson_datasets(const double* mu, int nbins, int64_t ndatasets, 
  *   P_out: device (or pinned host) [nL][n] of double (GNA_FP64) or float (mixed)
  * n = 0 is valid and launches nothing.  Returns GNA_EINVAL for NULL
  * pointers, for E or P_out that the device cannot address (host memory that
- * is neither page-locked nor coherently accessible), or an unknown
- * precision; GNA_ESHAPE for n < 0 or bad nL.
+ * is neither page-locked nor coherently accessible) or that is not aligned to
+ * its element type, or an unknown precision; GNA_ESHAPE for n < 0 or bad nL.
  */
 gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, const gna_osc* p,
                           gna_precision prec, void* P_out, void* stream);
@@ -181,7 +181,8 @@ gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, c
  * synchronised.  Staging memory comes from the stream-ordered allocator and
  * goes back to it on `stream`.  The result equals gna_oscprob_ee's bit for
  * bit.  GNA_EINVAL for NULL pointers, host memory that is not page-locked
- * (device memory included) or an unknown precision; GNA_ESHAPE for n < 0,
+ * (device memory included) or not aligned to its element type, or an unknown
+ * precision; GNA_ESHAPE for n < 0,
  * chunk < 0 or bad nL; GNA_ECUDA if a copy or launch could not be queued.
  */
 gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* L, int nL, const gna_osc* p,

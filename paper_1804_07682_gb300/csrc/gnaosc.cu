@@ -500,6 +500,8 @@ gna_status gna_gl_nodes(int n, double* x, double* w, void* stream) {
 // memory, page-locked host memory mapped at the same address (unified
 // addressing), or ordinary host memory where the device reports coherent access
 // to pageable memory.  Anything else is refused before a launch could fault.
+static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
+
 static bool device_accessible(const void* ptr) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
@@ -551,6 +553,8 @@ gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, c
     if (n == 0) return GNA_OK;
     if (!E || !P_out) return GNA_EINVAL;
     if (!device_accessible(E) || !device_accessible(P_out)) return GNA_EINVAL;
+    if (!aligned(E, sizeof(double)) || !aligned(P_out, prec == GNA_FP64 ? sizeof(double) : sizeof(float)))
+        return GNA_EINVAL;
     OscConst oc;
     if (ee_constants(L, nL, p, oc) != GNA_OK) return GNA_EINVAL;
     cudaError_t e = launch_oscprob(E, n, oc, prec, P_out, (cudaStream_t)stream);
@@ -603,6 +607,8 @@ gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* 
         }
         if (at.type != cudaMemoryTypeHost) return GNA_EINVAL;  // page-locked host memory only
     }
+    if (!aligned(E_host, sizeof(double)) || !aligned(P_host, prec == GNA_FP64 ? sizeof(double) : sizeof(float)))
+        return GNA_EINVAL;
     OscConst oc;
     if (ee_constants(L, nL, p, oc) != GNA_OK) return GNA_EINVAL;
     if (chunk == 0) chunk = std::max<int64_t>(int64_t(1) << 16, (n + 7) / 8);
@@ -610,7 +616,10 @@ gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* 
     const size_t esz = prec == GNA_FP64 ? sizeof(double) : sizeof(float);
     const int64_t nchunks = (n + chunk - 1) / chunk;
     const int nslots = (int)std::min<int64_t>(kStages, nchunks);
-    const size_t e_bytes = size_t(chunk) * sizeof(double), p_bytes = size_t(chunk) * nL * esz;
+    // every staging buffer starts on a 256-byte boundary (element alignment of
+    // the kernels' loads and stores, whatever chunk and nL are)
+    auto round256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t e_bytes = round256(size_t(chunk) * sizeof(double)), p_bytes = round256(size_t(chunk) * nL * esz);
     StageStreams ss;
     if (stage_streams(ss) != cudaSuccess) return GNA_ECUDA;
     cudaStream_t cs = (cudaStream_t)stream;
@@ -683,6 +692,8 @@ gna_status gna_oscprob(const double* E, int64_t n, const double* L, int nL, int 
     if (n == 0) return GNA_OK;
     if (!E || !P_out) return GNA_EINVAL;
     if (!device_accessible(E) || !device_accessible(P_out)) return GNA_EINVAL;
+    if (!aligned(E, sizeof(double)) || !aligned(P_out, prec == GNA_FP64 ? sizeof(double) : sizeof(float)))
+        return GNA_EINVAL;
     // V = U or U*; X_ij = V*_ai V_bi V_aj V*_bj for (i, j) = (2, 1), (3, 1), (3, 2)
     auto V = [&](int a, int i) {
         return std::complex<double>(ure[3 * a + i], anti ? -uim[3 * a + i] : uim[3 * a + i]);

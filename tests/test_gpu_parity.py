@@ -124,6 +124,18 @@ def test_oscprob_staged_refuses_unpinned(api):
                                          L.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, ctypes.byref(p),
                                          0, ctypes.c_void_p(Pd.data_ptr()), 0, None)
     assert code == 1  # GNA_EINVAL
+    # and pointers that are not aligned to their element type (refused on the
+    # host, before any launch)
+    Eh = torch.linspace(1.0, 10.0, 101, dtype=torch.float64).pin_memory()
+    Ph = torch.empty(1, 101, dtype=torch.float64).pin_memory()
+    Lp = L.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    code = N.lib().gna_oscprob_ee_staged(ctypes.c_void_p(Eh.data_ptr() + 4), 100, Lp, 1, ctypes.byref(p), 0,
+                                         ctypes.c_void_p(Ph.data_ptr()), 0, None)
+    assert code == 1
+    Ed = torch.linspace(1.0, 10.0, 101, dtype=torch.float64, device="cuda")
+    code = N.lib().gna_oscprob_ee(ctypes.c_void_p(Ed.data_ptr() + 4), 100, Lp, 1, ctypes.byref(p), 0,
+                                  ctypes.c_void_p(Pd.data_ptr()), None)
+    assert code == 1
 
 
 def test_oscprob_edge_cases(api):

@@ -178,8 +178,9 @@ gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, c
  *   L, nL, p, prec: as for gna_oscprob_ee
  * Asynchronous: the stages start after the work queued on `stream` and
  * `stream` waits for all of them, so P_host is complete once `stream` has
- * synchronised.  Staging memory comes from the stream-ordered allocator and
- * goes back to it on `stream`.  The result equals gna_oscprob_ee's bit for
+ * synchronised.  The stages' streams and staging buffers are kept per device
+ * for the life of the process (a buffer grows to the largest chunk asked
+ * for); calls are serialised.  The result equals gna_oscprob_ee's bit for
  * bit.  GNA_EINVAL for NULL pointers, host memory that is not page-locked
  * (device memory included) or not aligned to its element type, or an unknown
  * precision; GNA_ESHAPE for n < 0,

@@ -562,32 +562,45 @@ gna_status gna_oscprob_ee(const double* E, int64_t n, const double* L, int nL, c
 }
 
 namespace {
-// Copy/compute streams of the staged transfer pipeline, created once per device.
+// State of the staged transfer pipeline, one per device and kept for the
+// process: a stream per stage, the events that fork the stages from and join
+// them back into the caller's stream, and each stage's staging buffer.  A
+// buffer is only touched by work on its own stage's stream, so stream order
+// alone keeps one call's chunks from overwriting another's; growing it frees
+// the old one in that same order.  The mutex serialises enqueueing.
 constexpr int kStages = 3;
-struct StageStreams {
-    cudaStream_t s[kStages];
+struct StageState {
+    cudaStream_t s[kStages] = {};
+    cudaEvent_t fork = nullptr, join[kStages] = {};
+    char* buf[kStages] = {};
+    size_t cap[kStages] = {};
 };
 std::mutex g_stage_mu;
-std::map<int, StageStreams> g_stage_streams;
+std::map<int, StageState> g_stage;
 
-cudaError_t stage_streams(StageStreams& out) {
+cudaError_t stage_state(StageState*& out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(g_stage_mu);
-    auto it = g_stage_streams.find(dev);
-    if (it == g_stage_streams.end()) {
-        StageStreams ss{};
-        for (int j = 0; j < kStages; j++) {
-            e = cudaStreamCreateWithFlags(&ss.s[j], cudaStreamNonBlocking);
-            if (e != cudaSuccess) {
-                for (int i = 0; i < j; i++) cudaStreamDestroy(ss.s[i]);
-                return e;
-            }
+    auto it = g_stage.find(dev);
+    if (it == g_stage.end()) {
+        StageState st;
+        e = cudaEventCreateWithFlags(&st.fork, cudaEventDisableTiming);
+        for (int j = 0; e == cudaSuccess && j < kStages; j++) {
+            e = cudaStreamCreateWithFlags(&st.s[j], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.join[j], cudaEventDisableTiming);
         }
-        it = g_stage_streams.emplace(dev, ss).first;
+        if (e != cudaSuccess) {
+            if (st.fork) cudaEventDestroy(st.fork);
+            for (int j = 0; j < kStages; j++) {
+                if (st.s[j]) cudaStreamDestroy(st.s[j]);
+                if (st.join[j]) cudaEventDestroy(st.join[j]);
+            }
+            return e;
+        }
+        it = g_stage.emplace(dev, st).first;
     }
-    out = it->second;
+    out = &it->second;
     return cudaSuccess;
 }
 }  // namespace
@@ -616,24 +629,28 @@ gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* 
     const size_t esz = prec == GNA_FP64 ? sizeof(double) : sizeof(float);
     const int64_t nchunks = (n + chunk - 1) / chunk;
     const int nslots = (int)std::min<int64_t>(kStages, nchunks);
-    // every staging buffer starts on a 256-byte boundary (element alignment of
-    // the kernels' loads and stores, whatever chunk and nL are)
+    // each staging buffer, and P's part of it, starts on a 256-byte boundary
+    // (element alignment of the kernels' loads and stores, whatever chunk and nL are)
     auto round256 = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t e_bytes = round256(size_t(chunk) * sizeof(double)), p_bytes = round256(size_t(chunk) * nL * esz);
-    StageStreams ss;
-    if (stage_streams(ss) != cudaSuccess) return GNA_ECUDA;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    StageState* st = nullptr;
+    if (stage_state(st) != cudaSuccess) return GNA_ECUDA;
     cudaStream_t cs = (cudaStream_t)stream;
-    char* buf = nullptr;
-    cudaEvent_t fork = nullptr, join[kStages] = {};
-    cudaError_t e = cudaMallocAsync((void**)&buf, nslots * (e_bytes + p_bytes), cs);
-    if (e != cudaSuccess) return GNA_ECUDA;
-    bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventRecord(fork, cs) == cudaSuccess;
+    if (cudaEventRecord(st->fork, cs) != cudaSuccess) return GNA_ECUDA;
+    bool ok = true;
     int forked = 0;
     for (int j = 0; ok && j < nslots; j++) {
-        ok = cudaEventCreateWithFlags(&join[j], cudaEventDisableTiming) == cudaSuccess &&
-             cudaStreamWaitEvent(ss.s[j], fork, 0) == cudaSuccess;
-        if (ok) forked = j + 1;
+        ok = cudaStreamWaitEvent(st->s[j], st->fork, 0) == cudaSuccess;
+        if (!ok) break;
+        forked = j + 1;
+        if (st->cap[j] < e_bytes + p_bytes) {
+            if (st->buf[j]) cudaFreeAsync(st->buf[j], st->s[j]);
+            st->buf[j] = nullptr;
+            st->cap[j] = 0;
+            ok = cudaMallocAsync((void**)&st->buf[j], e_bytes + p_bytes, st->s[j]) == cudaSuccess;
+            if (ok) st->cap[j] = e_bytes + p_bytes;
+        }
     }
     // chunk c on stage c mod nslots: upload its energies, evaluate, download its
     // nL probability rows; the stages overlap the upload of one chunk with the
@@ -641,22 +658,17 @@ gna_status gna_oscprob_ee_staged(const double* E_host, int64_t n, const double* 
     for (int64_t c = 0; ok && c < nchunks; c++) {
         const int j = (int)(c % nslots);
         const int64_t k0 = c * chunk, len = std::min(chunk, n - k0);
-        double* dE = (double*)(buf + j * (e_bytes + p_bytes));
-        char* dP = (char*)dE + e_bytes;
-        ok = cudaMemcpyAsync(dE, E_host + k0, len * sizeof(double), cudaMemcpyHostToDevice, ss.s[j]) == cudaSuccess &&
-             launch_oscprob(dE, len, oc, prec, dP, ss.s[j]) == cudaSuccess &&
+        double* dE = (double*)st->buf[j];
+        char* dP = st->buf[j] + e_bytes;
+        ok = cudaMemcpyAsync(dE, E_host + k0, len * sizeof(double), cudaMemcpyHostToDevice, st->s[j]) == cudaSuccess &&
+             launch_oscprob(dE, len, oc, prec, dP, st->s[j]) == cudaSuccess &&
              cudaMemcpy2DAsync((char*)P_host + k0 * esz, n * esz, dP, len * esz, len * esz, nL,
-                               cudaMemcpyDeviceToHost, ss.s[j]) == cudaSuccess;
+                               cudaMemcpyDeviceToHost, st->s[j]) == cudaSuccess;
     }
-    // join the stages back into the caller's stream (also after a failed
-    // enqueue, so that the staging memory is released behind what was queued)
+    // join the stages back into the caller's stream (also after a failed enqueue)
     for (int j = 0; j < forked; j++)
-        if (cudaEventRecord(join[j], ss.s[j]) != cudaSuccess || cudaStreamWaitEvent(cs, join[j], 0) != cudaSuccess)
+        if (cudaEventRecord(st->join[j], st->s[j]) != cudaSuccess || cudaStreamWaitEvent(cs, st->join[j], 0) != cudaSuccess)
             ok = false;
-    if (cudaFreeAsync(buf, cs) != cudaSuccess) ok = false;
-    if (fork) cudaEventDestroy(fork);
-    for (int j = 0; j < kStages; j++)
-        if (join[j]) cudaEventDestroy(join[j]);
     return ok ? GNA_OK : GNA_ECUDA;
 }
 

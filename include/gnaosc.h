@@ -135,11 +135,14 @@ gna_status gna_gl_nodes(int n, double* x, double* w, void* stream);
  * j / 2^32, q) under the key (seed mod 2^32, seed / 2^32), one 53-bit
  * uniform u = ((x0 >> 5) 2^26 + (x1 >> 6)) 2^-53, and inversion: the
  * smallest k with F(k) >= u, p_0 = e^-m (computed on the host), p_k =
- * p_{k-1} m / k, at most 10 m + 100 steps, each operation rounded once.
- * Draws do not depend on the launch shape; the cost is O(mu) per sample.
+ * p_{k-1} m / k, k at most 10 m + 100, each operation rounded once.  The
+ * cumulative F is tabulated once per bin and bisected per sample, so the
+ * cost is O(m) per bin plus O(log m) per sample.  Draws do not depend on the
+ * launch shape.
  *   mu:       host [nbins], each in [0, 1e7] (GNA_EINVAL otherwise)
  *   data_out: device [ndatasets][nbins] double (integer values)
- * Uses a stream-ordered temporary of 2 nbins doubles and nbins ints.
+ * Uses a stream-ordered temporary: 3 nbins doubles and ints, and the tables
+ * (10 m + 101 doubles per bin, bin ranges of at most 2^24 entries at a time).
  */
 gna_status gna_poisson_datasets(const double* mu, int nbins, int64_t ndatasets, uint64_t seed, double* data_out,
                                 void* stream);

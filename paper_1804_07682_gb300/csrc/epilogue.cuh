@@ -44,7 +44,7 @@ struct EpiArgs {
     float2* binvals;       // [npts][nbins][NBV] scratch (double-float values)
     int NBV;               // 1 (chi2), 5 (+ gradient), 15 (+ J^T W J)
     const double* sumW;    // [ngrids][nbins] summed FP32 node weights (mixed modes)
-    int shared_grid;
+    const int* gid;        // [npts] grid of each point, or NULL: every point uses grid 0
     float wsum_lo;               // exact sum of the FP32 weights - the kernel's constant term
     float om_delta[GNA_NLMAX];   // omega_r - om_r (corrections ~1e-8 relative: FP32 suffices)
     double* chi2;          // [npts]
@@ -89,7 +89,7 @@ __device__ __forceinline__ BinIn bin_inputs(const EpiArgs& a, int p, int i) {
     BinIn in;
     in.d = a.data[a.data_per_point ? idx : i];
     in.e = a.eta ? a.eta[i] : 0.0;
-    in.sumw = a.sumW ? a.sumW[(a.shared_grid ? 0 : (int64_t)p * a.nbins) + i] : 0.0;
+    in.sumw = a.sumW ? a.sumW[(a.gid ? (int64_t)a.gid[p] * a.nbins : 0) + i] : 0.0;
     return in;
 }
 

@@ -288,7 +288,7 @@ struct BinArgs {
     const float4* grid;
     const int64_t* goff;  // [ngrids] float4 offset of each grid
     const int* gn;        // [ngrids] Gauss-Legendre order of each grid
-    int shared_grid;      // 1: every point uses grid 0
+    const int* gid;       // [npts] grid of each point, or NULL: every point uses grid 0
     const int* tasks;     // [ntasks] p * ngroups + b, in execution order
     int ntasks, ngroups, nbins;
     const PointConst* pcs;
@@ -327,9 +327,9 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
             p = task / a.ngroups;
             b = task - p * a.ngroups;
             k0 = 0;
-            n = a.gn[a.shared_grid ? 0 : p];
+            n = a.gn[a.gid ? a.gid[p] : 0];
         }
-        const int gi = a.shared_grid ? 0 : p;
+        const int gi = a.gid ? a.gid[p] : 0;
         const int kn = min(n, k0 + (a.S > 1 ? a.L : n)) - k0;  // nodes of this task per lane
         if (p != last_p) {
             m.load(a.pcs + p, a.bc);

@@ -139,7 +139,7 @@ struct BinArgs64 {
     const double2* grid;
     const int64_t* goff;
     const int* gn;
-    int shared_grid;
+    const int* gid;  // [npts] grid of each point, or NULL: every point uses grid 0
     const int* tasks;
     int ntasks, ngroups, nbins;
     const PointConst* pcs;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_fused64_bins(BinArgs64 a) {
         const int task = a.tasks[t];
         const int p = task / a.ngroups;
         const int b = task - p * a.ngroups;
-        const int gi = a.shared_grid ? 0 : p;
+        const int gi = a.gid ? a.gid[p] : 0;
         const int n = a.gn[gi];
         if (p != last_p) {
             m.load(a.pcs + p, a.bc);

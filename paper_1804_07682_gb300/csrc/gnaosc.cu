@@ -102,6 +102,7 @@ struct gna_plan {
     int64_t grid_len = 0, total_nodes = 0;
     int64_t* d_goff = nullptr;
     int* d_gn = nullptr;
+    int* d_gid = nullptr;  // [npts] grid of each point (NULL: one grid for all)
     int ngrids = 0, ngroups = 0;
     int* d_tasks = nullptr;
     int ntasks = 0;
@@ -340,7 +341,7 @@ EpiArgs make_epi(const gna_plan* plan, const EvalReq& q, bool grad, bool spec, i
     ea.binvals = plan->d_binvals;
     ea.NBV = q.H ? 15 : (grad ? 5 : 1);
     ea.sumW = plan->d_sumW;
-    ea.shared_grid = plan->ngrids == 1;
+    ea.gid = plan->d_gid;
     // the kernel's constant term is wsum; the exact one is sum_r om_r when the
     // per-baseline sums carry the weight correction (or one baseline), else
     // sum_r (om_r + omlo_r)
@@ -403,7 +404,7 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     } else if (plan->mapping == MAP_SLICES) {
         const int g = grid_size(plan, grad, spec, ssh.ntasks);
         const bool sliced = ssh.S > 1;
-        BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, ssh.ntasks,
+        BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, ssh.ntasks,
                   plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea,
                   ssh.S, ssh.L, sliced ? plan->d_slices : nullptr};
         CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
@@ -414,11 +415,11 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     } else {
         const int g = grid_size(plan, grad, spec, plan->ntasks);
         if (plan->ph < 2) {
-            BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+            BinArgs a{plan->grid_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, plan->ntasks,
                       plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, 1, 0, nullptr};
             CU(dispatch_bins(plan->ph, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         } else {
-            BinArgs64 a{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->ngrids == 1, plan->d_tasks, plan->ntasks,
+            BinArgs64 a{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, plan->ntasks,
                         plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea};
             CU(dispatch_bins(2, plan->nl_inst, grad, spec, &a, g, plan->block, s));
         }
@@ -839,23 +840,31 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
                             (int64_t)d->nbins * plan->n_uniform <= (1LL << 26);
     plan->has_split = plan->mapping == MAP_SPLIT || (!forced && small) || keep_split;
     plan->has_bins = plan->mapping == MAP_BINS || plan->mapping == MAP_SLICES || (!forced && small);
-    const bool shared = plan->uniform;
-    plan->ngrids = shared ? 1 : d->npts;
+    // one grid per distinct node count: the bins and weights depend on nothing
+    // else, so points with the same count share one grid (read once from HBM
+    // and from L2 by the points that follow it in the task order)
+    std::vector<int> gn(plan->counts.begin(), plan->counts.end());
+    std::sort(gn.begin(), gn.end());
+    gn.erase(std::unique(gn.begin(), gn.end()), gn.end());
+    plan->ngrids = (int)gn.size();
+    std::vector<int> gid(d->npts);
+    for (int p = 0; p < d->npts; p++)
+        gid[p] = (int)(std::lower_bound(gn.begin(), gn.end(), plan->counts[p]) - gn.begin());
     const int nbins_pad = ngroups * 32;
     // grid offsets of the bins layout (the split layout is one bin-major grid)
     std::vector<int64_t> goff(plan->ngrids);
-    std::vector<int> gn(plan->ngrids);
     int64_t off = 0;
     for (int g = 0; g < plan->ngrids; g++) {
         goff[g] = off;
-        gn[g] = plan->counts[g];
         off += (int64_t)nbins_pad * gn[g];
     }
     const int64_t len_bins = off;
     const int64_t len_split = (int64_t)d->nbins * plan->n_uniform;
     plan->grid_len = plan->has_bins ? len_bins : len_split;
-    plan->total_nodes = 0;
-    for (int g = 0; g < plan->ngrids; g++) plan->total_nodes += (int64_t)d->nbins * gn[g];
+    plan->total_nodes = 0;  // node evaluations per evaluation of all points (per point if uniform)
+    if (plan->uniform) plan->total_nodes = (int64_t)d->nbins * plan->n_uniform;
+    else
+        for (int p = 0; p < d->npts; p++) plan->total_nodes += (int64_t)d->nbins * plan->counts[p];
     const bool want64 = plan->ph == 2;
     const bool want_plain = (d->flags & GNA_PLAN_WITH_PLAIN) != 0;
     if (want_plain && !plan->uniform) return fail(plan, GNA_EINVAL, "the plain chain needs equal node counts");
@@ -875,6 +884,10 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     TRY(dalloc(plan, &plan->d_gn, plan->ngrids));
     CU(cudaMemcpyAsync(plan->d_goff, goff.data(), sizeof(int64_t) * plan->ngrids, cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(plan->d_gn, gn.data(), sizeof(int) * plan->ngrids, cudaMemcpyHostToDevice, s));
+    if (plan->ngrids > 1) {
+        TRY(dalloc(plan, &plan->d_gid, d->npts));
+        CU(cudaMemcpyAsync(plan->d_gid, gid.data(), sizeof(int) * d->npts, cudaMemcpyHostToDevice, s));
+    }
     // Gauss-Legendre rules per distinct order
     std::vector<int> orders(gn.begin(), gn.end());
     std::sort(orders.begin(), orders.end());

@@ -226,7 +226,7 @@ extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, 
     ea.binvals = reinterpret_cast<float2*>(base + kOffBin);
     ea.NBV = 5;
     ea.sumW = a.sumW;
-    ea.shared_grid = 1;
+    ea.gid = nullptr;
     ea.wsum_lo = (float)((nl_inst == 1) ? bc.wsum_lo : fall - (double)bc.wsum);
     ea.chi2 = chi2;
     ea.grad = grad;

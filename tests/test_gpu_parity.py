@@ -325,6 +325,19 @@ def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):
         check_chain(api, case, prec, mapping)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
+def test_points_sharing_grids(api, prec):
+    # points with equal node counts share one energy grid on the device; the
+    # counts are interleaved so that a shared grid serves points far apart in
+    # the point order, and the largest count is held by a single point
+    rng = np.random.default_rng(5)
+    counts = np.array([7, 12, 7, 30, 12, 7, 5, 30, 12, 41])
+    theta = np.tile(np.array(wl.TRUTH), (counts.size, 1)) * rng.uniform(0.95, 1.05, size=(counts.size, 4))
+    w = wl.Workload("shared_grids", np.linspace(1.8, 8.0, 71), 0, np.array([52.5, 53.1]), theta, wl.POISSON,
+                    node_counts=counts)
+    check_chain(api, Case(w), prec)
+
+
 def test_plain_chain_matches_oracle(api):
     case = get_case("reactor8_40x3000")
     w = case.w

@@ -62,8 +62,8 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
 TRAFFIC_CAPTURE = {
     "split": {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
               "bytes": 265113600 + 4114176},
-    "slices": {"sources_sha256": "2c38c9bd88d1844ab9261339b3f69e62c02dffd7e8abbd2ee6da78c02cc33a8d",
-               "bytes": 268521984 + 4973056 + 8176128},
+    "slices": {"sources_sha256": "a7159a9d2817b6941ab11b6b92e3fecc30531eb81a15b5d62a927d4c92bf7dda",
+               "bytes": 268655360 + 5216768 + 8175872},
 }
 KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
                   "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h",

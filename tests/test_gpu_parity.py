@@ -542,6 +542,16 @@ def test_pseudo_data_matches_oracle_bit_for_bit(api):
     assert api.poisson_datasets([1.0], 0, 1).numel() == 0
 
 
+def test_pseudo_data_many_bins_over_several_tables(api):
+    # 4000 bins of mean 500 need 20.4 M table entries: the bins are drawn in
+    # two ranges of at most 2^24 entries; the draws are the same bit for bit
+    rng = np.random.default_rng(8)
+    mu = np.full(4000, 500.0)
+    mu[::7] = rng.uniform(0.0, 1500.0, mu[::7].size)
+    dev_data = api.poisson_datasets(mu, 3, 11).cpu().numpy()
+    assert np.array_equal(dev_data, oracle.pseudo_data(mu, 3, 11))
+
+
 def test_device_status_flags_unphysical_points(api):
     # the parameters live on the device; a point with s2 > 1 is found there
     # and reported by status(), which then clears

@@ -616,11 +616,20 @@ def main():
 
         oracle.chain(w.edges[:2], w.nodes_per_bin, w.L, w.theta[0], 1.0, np.full(1, 100.0), w.kind)
         t0 = time.perf_counter()
-        oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], N, data_np, w.kind)
+        ref = oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], N, data_np, w.kind)
         dt = time.perf_counter() - t0
         cpu = {"value": 1.0 / dt, "unit": "evals/s", "cores": oracle.threads(), "kind": "oracle",
                "sample": "one full evaluation (%d bins x %d nodes x %d baselines, with gradient) in %.2f s on %d threads"
                          % (w.nbins, w.nodes_per_bin, w.nL, dt, oracle.threads())}
+        # the benchmarked path's error against that oracle evaluation, every output
+        go = plan.eval(params, data, grad=True, spectra=True, mu=True)
+        torch.cuda.synchronize()
+        rmax = lambda a, b: float(np.max(np.abs(a - b) / np.abs(b)))
+        g = go["grad"][0].cpu().numpy()
+        cpu["gpu_error_vs_oracle"] = {
+            "chi2": rmax(go["chi2"][0].item(), ref["chi2"]), "mu": rmax(go["mu"][0].cpu().numpy(), ref["mu"]),
+            "spectra": rmax(go["spectra"][0].cpu().numpy(), ref["mu_rb"]),
+            "grad_normwise": float(np.linalg.norm(g - ref["grad"][:4]) / np.linalg.norm(ref["grad"][:4]))}
 
     side = None if args.no_side else side_workloads(api, torch, device, args)
     if side is not None and cpu is not None:

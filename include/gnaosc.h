@@ -75,7 +75,7 @@ typedef struct {
     const double* edges;        /* host [nbins+1], MeV, strictly increasing, > 0 */
     int nodes_per_bin;          /* Gauss-Legendre order of every point when node_counts == NULL; 1..65536 */
     int npts;                   /* parameter points evaluated per call; >= 1 */
-    const int32_t* node_counts; /* host [npts] per-point order (each point its own grid), or NULL */
+    const int32_t* node_counts; /* host [npts] per-point order (points of equal order share a grid), or NULL */
     int nL;                     /* baselines, 1..16 */
     const double* L;            /* host [nL], km, > 0 */
     const double* Lweight;      /* host [nL] combination weights, or NULL for 1/L^2 normalised to sum 1 */

@@ -284,9 +284,10 @@ gna_status gna_chain_eval_cached(gna_plan* plan, const double* eta, double sigma
  * to the device in one transfer, evaluates, copies chi2 [npts], grad
  * [npts][4] (if grad != NULL) and spectra [npts][nL][nbins] (if spectra !=
  * NULL; GNA_ESHAPE when that exceeds 2^24 values) back in one transfer,
- * synchronises the stream and unpacks them into the caller's buffers.  With
- * graph mode on (gna_plan_set_graph) the transfer-evaluate-transfer sequence
- * is replayed as one graph.  Any host memory is accepted. */
+ * waits for it and unpacks them into the caller's buffers.  The evaluation
+ * runs on `stream` (replayed as one graph with graph mode on,
+ * gna_plan_set_graph); the two transfers run on two plan-owned copy streams,
+ * joined to it by events.  Any host memory is accepted. */
 gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
                                const double* data, int data_per_point, double* chi2, double* grad, double* spectra,
                                void* stream);
@@ -294,9 +295,13 @@ gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const doub
 /* gna_chain_eval_host_async / gna_chain_eval_host_wait: gna_chain_eval_host
  * in two halves, so that consecutive evaluations overlap the host's packing,
  * launching and unpacking with the device's work.  _async packs the inputs
- * into one of the plan's two pinned staging slots, enqueues transfer ->
- * evaluation -> transfer on `stream` (outputs: chi2, and the gradient and the
- * spectra when grad / spectra != 0) and returns a ticket at once; _wait
+ * into one of the plan's two pinned staging slots (each with its own device
+ * inputs and outputs), enqueues the upload on a plan-owned copy stream, the
+ * evaluation on `stream` after it, and the download on a second copy stream
+ * after the evaluation (outputs: chi2, and the gradient and the spectra when
+ * grad / spectra != 0), and returns a ticket at once: the upload of one
+ * evaluation and the download of the other overlap the evaluation running on
+ * `stream`.  _wait
  * blocks until that evaluation is done and unpacks its results into the
  * caller's buffers (any of them may be NULL).  At most two evaluations may be
  * outstanding: _async returns GNA_ESTATE while the slot it needs holds a
@@ -361,10 +366,13 @@ gna_status gna_plan_set_graph(gna_plan* plan, int on);
  * call (graph replays count the kernels inside the graph). */
 int gna_plan_kernel_launches(const gna_plan* plan);
 
-/* gna_plan_profile: with on != 0, every evaluation outside graph capture
- * records a pair of CUDA events on its stream around the fused node kernel
- * (with the slice mapping: the node kernel and the slice reduction; up to
- * 8192 pairs).  gna_plan_profile_read synchronises those events and
+/* gna_plan_profile: with on = k >= 1, every k-th evaluation outside graph
+ * capture (the first, then every k-th after it) records a pair of CUDA events
+ * on its stream around the fused node kernel (with the slice mapping: the
+ * node kernel and the slice reduction; up to 8192 pairs); on = 0 switches it
+ * off, on < 0 is GNA_EINVAL.  Events between two kernels keep the second from
+ * starting while the first drains, so a period above 1 leaves most
+ * evaluations undisturbed.  gna_plan_profile_read synchronises those events and
  * returns the summed kernel time in ms and the number of timed launches,
  * then clears them. */
 gna_status gna_plan_profile(gna_plan* plan, int on);

@@ -256,9 +256,10 @@ class Plan:
     def set_graph(self, on: bool):
         self._check(self._lib.gna_plan_set_graph(self._h, int(bool(on))), "set_graph")
 
-    def profile(self, on: bool):
-        """Record CUDA events around the fused node kernel of each evaluation."""
-        self._check(self._lib.gna_plan_profile(self._h, int(bool(on))), "profile")
+    def profile(self, on):
+        """Record CUDA events around the fused node kernel of every evaluation
+        (on = True or 1), of every k-th one (on = k), or not (on = False or 0)."""
+        self._check(self._lib.gna_plan_profile(self._h, int(on)), "profile")
 
     def profile_read(self):
         """(summed fused-kernel ms, timed launches) since the last read."""

@@ -154,24 +154,33 @@ struct gna_plan {
     bool profile = false;
     std::vector<cudaEvent_t> prof_ev;  // pairs
     int prof_n = 0;
+    int prof_every = 1;      // time every prof_every-th evaluation
+    int64_t prof_seen = 0;   // evaluations seen since profiling was switched on
     // packed staging of the host-buffer call: inputs [params | data | eta],
     // outputs [chi2 | grad | spectra], pinned on the host, contiguous on the device
     // host-buffer evaluations: two pinned staging slots (an evaluation packs
     // slot k while the one before it may still be copying from slot k ^ 1),
     // one device staging pair (the stream serialises its use)
+    // Host-buffer evaluations: two slots, each with pinned host staging and its
+    // own device inputs and outputs, so that the upload of one evaluation (on
+    // cp_in) and the download of another (on cp_out) overlap the evaluation
+    // running on the caller's stream.
     struct HostSlot {
         double* h_in = nullptr;
         double* h_out = nullptr;
+        double* d_in = nullptr;
+        double* d_out = nullptr;
         cudaGraphExec_t exec = nullptr;
         GraphKey key;
-        cudaEvent_t done = nullptr;
+        cudaEvent_t in_ready = nullptr;  // upload complete (cp_in)
+        cudaEvent_t computed = nullptr;  // evaluation complete (caller's stream)
+        cudaEvent_t done = nullptr;      // download complete (cp_out)
         int64_t ticket = -1;  // evaluation whose results the slot holds
         bool pending = false; // enqueued, results not yet taken
         bool grad = false, spectra = false;
     } hs[2];
     int64_t next_ticket = 0;
-    double* d_in = nullptr;
-    double* d_out = nullptr;
+    cudaStream_t cp_in = nullptr, cp_out = nullptr;
     size_t in_cap = 0, out_cap = 0;
     double* d_sumW = nullptr;  // [ngrids][nbins]
     double wsum_all_lo = 0.0;  // sum_r (om_r + omlo_r) - wsum: constant term when the weights enter as hi + lo
@@ -388,7 +397,9 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
     ea.binsums = q.H ? nullptr : plan->d_binsums;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(s, &cap));
-    const bool timed = plan->profile && cap == cudaStreamCaptureStatusNone && plan->prof_n < (int)plan->prof_ev.size() / 2;
+    bool timed = false;
+    if (plan->profile && cap == cudaStreamCaptureStatusNone)
+        timed = (plan->prof_seen++ % plan->prof_every) == 0 && plan->prof_n < (int)plan->prof_ev.size() / 2;
     if (timed) CU(cudaEventRecord(plan->prof_ev[2 * plan->prof_n], s));
     if (plan->mapping == MAP_SPLIT) {
         if (plan->ph < 2) {
@@ -741,13 +752,18 @@ gna_status gna_plan_destroy(gna_plan* plan) {
     if (!plan) return GNA_OK;
     destroy_graph(plan);
     destroy_profile(plan);
+    for (cudaStream_t cs : {plan->cp_in, plan->cp_out})
+        if (cs) cudaStreamSynchronize(cs);
     for (auto& h : plan->hs) {
         if (h.exec) cudaGraphExecDestroy(h.exec);
-        if (h.done) cudaEventDestroy(h.done);
+        for (cudaEvent_t ev : {h.in_ready, h.computed, h.done})
+            if (ev) cudaEventDestroy(ev);
         if (h.h_in) cudaFreeHost(h.h_in);
         if (h.h_out) cudaFreeHost(h.h_out);
     }
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    if (plan->cp_in) cudaStreamDestroy(plan->cp_in);
+    if (plan->cp_out) cudaStreamDestroy(plan->cp_out);
     for (void* v : plan->allocs) cudaFree(v);
     delete plan;
     return GNA_OK;
@@ -978,16 +994,19 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     plan->in_cap = (size_t)d->npts * 4 + (size_t)plan->max_datasets * d->nbins + d->nbins;
     plan->out_cap = (size_t)d->npts * 5;
     if ((int64_t)d->npts * d->nL * d->nbins <= (1LL << 24)) plan->out_cap += (size_t)d->npts * d->nL * d->nbins;
-    TRY(dalloc(plan, &plan->d_in, plan->in_cap));
-    TRY(dalloc(plan, &plan->d_out, plan->out_cap));
+    CU(cudaStreamCreateWithFlags(&plan->cp_in, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&plan->cp_out, cudaStreamNonBlocking));
     for (auto& h : plan->hs) {
+        TRY(dalloc(plan, &h.d_in, plan->in_cap));
+        TRY(dalloc(plan, &h.d_out, plan->out_cap));
         cudaError_t e1 = cudaMallocHost(&h.h_in, plan->in_cap * sizeof(double));
         cudaError_t e2 = cudaMallocHost(&h.h_out, plan->out_cap * sizeof(double));
-        cudaError_t e3 = cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
             cudaGetLastError();
             return fail(plan, GNA_ENOMEM, "pinned staging of %zu + %zu doubles", plan->in_cap, plan->out_cap);
         }
+        for (cudaEvent_t* ev : {&h.in_ready, &h.computed, &h.done})
+            CU(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
     }
     TRY(dalloc(plan, &plan->d_lm, d->npts));
     TRY(dalloc(plan, &plan->d_status, 1));
@@ -1143,19 +1162,22 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
     if (eta) memcpy(h.h_in + n_par + n_dat, eta, n_eta * sizeof(double));
     const size_t n_in = n_par + n_dat + n_eta;
     const size_t n_out = (size_t)plan->npts * 5 + (spectra ? n_spec : 0);
-    double* d_par = plan->d_in;
-    double* d_dat = plan->d_in + n_par;
-    double* d_eta = eta ? plan->d_in + n_par + n_dat : nullptr;
-    EvalReq q{(const gna_osc*)d_par, d_eta, sigma_eta, d_dat, data_per_point, plan->d_out,
-              grad ? plan->d_out + plan->npts : nullptr, nullptr, nullptr,
-              spectra ? plan->d_out + (size_t)plan->npts * 5 : nullptr, nullptr};
-    // one H2D, the evaluation, one D2H: replayed as one graph in graph mode
-    auto enqueue_all = [&](cudaStream_t st, int* nl) -> gna_status {
-        CU(cudaMemcpyAsync(plan->d_in, h.h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, st));
-        TRY(enqueue_eval(plan, q, st, nl));
-        CU(cudaMemcpyAsync(h.h_out, plan->d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
-        return GNA_OK;
-    };
+    double* d_par = h.d_in;
+    double* d_dat = h.d_in + n_par;
+    double* d_eta = eta ? h.d_in + n_par + n_dat : nullptr;
+    EvalReq q{(const gna_osc*)d_par, d_eta, sigma_eta, d_dat, data_per_point, h.d_out,
+              grad ? h.d_out + plan->npts : nullptr, nullptr, nullptr,
+              spectra ? h.d_out + (size_t)plan->npts * 5 : nullptr, nullptr};
+    // upload on cp_in once the evaluation that last read this slot's inputs
+    // is done; it overlaps whatever the caller's stream is running
+    CU(cudaStreamWaitEvent(plan->cp_in, h.computed, 0));
+    CU(cudaMemcpyAsync(h.d_in, h.h_in, n_in * sizeof(double), cudaMemcpyHostToDevice, plan->cp_in));
+    CU(cudaEventRecord(h.in_ready, plan->cp_in));
+    // the evaluation on the caller's stream, after the upload and after the
+    // download of this slot's previous results
+    CU(cudaStreamWaitEvent(s, h.in_ready, 0));
+    CU(cudaStreamWaitEvent(s, h.done, 0));
+    auto enqueue_all = [&](cudaStream_t st, int* nl) -> gna_status { return enqueue_eval(plan, q, st, nl); };
     if (plan->use_graph) {
         double sig = sigma_eta;
         uintptr_t sigbits;
@@ -1193,7 +1215,11 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
     } else {
         TRY(enqueue_all(s, &plan->last_launches));
     }
-    CU(cudaEventRecord(h.done, s));
+    CU(cudaEventRecord(h.computed, s));
+    // download on cp_out after the evaluation; it overlaps the next one
+    CU(cudaStreamWaitEvent(plan->cp_out, h.computed, 0));
+    CU(cudaMemcpyAsync(h.h_out, h.d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, plan->cp_out));
+    CU(cudaEventRecord(h.done, plan->cp_out));
     h.ticket = t;
     h.pending = true;
     h.grad = grad != 0;
@@ -1435,10 +1461,13 @@ int gna_plan_kernel_launches(const gna_plan* plan) { return plan ? plan->last_la
 gna_status gna_plan_profile(gna_plan* plan, int on) {
     if (!plan) return GNA_EINVAL;
     destroy_profile(plan);
+    if (on < 0) return fail(plan, GNA_EINVAL, "profile period must be >= 0");
     if (on) {
         plan->prof_ev.resize(2 * 8192);
         for (auto& e : plan->prof_ev) CU(cudaEventCreate(&e));
         plan->profile = true;
+        plan->prof_every = on;
+        plan->prof_seen = 0;
     }
     return GNA_OK;
 }

@@ -350,6 +350,25 @@ def test_plain_chain_matches_oracle(api):
     assert normrel(out["grad"][0].cpu().numpy(), ref["grad"][:4]) < 1e-9
 
 
+def test_sampled_kernel_profiling(api):
+    case = get_case("reactor_200x50")
+    w = case.w
+    plan = make_plan(api, case, "ff")
+    p, d = plan.params_tensor(w.theta), dev(case.data)
+    plan.profile(3)  # evaluations 0, 3, 6 and 9 of ten are timed
+    for _ in range(10):
+        plan.eval(p, d, grad=True)
+    ms, n = plan.profile_read()
+    assert n == 4 and ms > 0.0
+    plan.profile(0)
+    plan.eval(p, d, grad=True)
+    assert plan.profile_read() == (0.0, 0)
+    from paper_1804_07682_gb300 import _native as N
+    with pytest.raises(N.GnaError):
+        plan.profile(-1)
+    plan.close()
+
+
 def test_graph_replay_and_host_buffers(api):
     case = get_case("reactor8_40x3000")
     w = case.w

@@ -27,7 +27,8 @@ def api():
 
 
 @pytest.mark.parametrize("tuning", [None, "mapping=split block=256 nodes=32", "mapping=split block=128 nodes=128",
-                                    "mapping=slices block=128 slice=108", "mapping=slices block=256 slice=1000"])
+                                    "mapping=slices block=256 slice=216", "mapping=slices block=128 slice=108",
+                                    "mapping=slices block=256 slice=1000"])
 def test_reactor8_full(api, tuning):
     w = wl.reactor8_1000x16384()
     case = _cached("reactor8", lambda: Case(w))

@@ -101,8 +101,11 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % index) if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d_%d.csv" % (index, os.getpid())
+        # the raw samples go to $BENCH_CLOCKS_DIR (if set) or the temporary directory
+        import tempfile
+
+        d = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, "bench_clocks_%d_%d.csv" % (index, os.getpid()))
 
     def start(self):
         try:

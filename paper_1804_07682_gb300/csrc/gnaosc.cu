@@ -508,25 +508,27 @@ gna_status gna_gl_nodes(int n, double* x, double* w, void* stream) {
     return e == cudaSuccess ? GNA_OK : GNA_ECUDA;
 }
 
-// Whether a kernel on the current device may dereference ptr: device or managed
-// memory, page-locked host memory mapped at the same address (unified
-// addressing), or ordinary host memory where the device reports coherent access
-// to pageable memory.  Anything else is refused before a launch could fault.
 static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
 
+// Whether a kernel on the current device may dereference ptr: memory of this
+// device, managed memory, page-locked host memory mapped at the same address
+// (unified addressing), or ordinary host memory where the device reports
+// coherent access to pageable memory.  Anything else (another device's
+// memory included) is refused before a launch could fault.
 static bool device_accessible(const void* ptr) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
     switch (at.type) {
-        case cudaMemoryTypeDevice:
+        case cudaMemoryTypeDevice: return at.device == dev;
         case cudaMemoryTypeManaged: return true;
         case cudaMemoryTypeHost: return at.devicePointer == ptr;
         default: {
-            int dev = 0, pageable = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess) return false;
+            int pageable = 0;
             if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return false;
             return pageable != 0;
         }

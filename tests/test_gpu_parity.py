@@ -325,6 +325,19 @@ def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):
         check_chain(api, case, prec, mapping)
 
 
+@pytest.mark.parametrize("nL", [3, 5, 12, 16])
+@pytest.mark.parametrize("prec,mapping", [("fp64", None), ("ff", "split"), ("ff", "bins"), ("ff", "slices")])
+def test_baseline_counts_between_instantiations(api, nL, prec, mapping):
+    # kernels exist for 1, 2, 4, 8 and 16 baselines; other counts run the next
+    # one up with zero-weight padding, and their per-baseline spectra must
+    # still be those of the real baselines only
+    rng = np.random.default_rng(nL)
+    L = np.sort(rng.uniform(0.5, 60.0, nL))
+    theta = np.array([wl.TRUTH]) * rng.uniform(0.97, 1.03, size=(1, 4))
+    w = wl.Workload("baselines_%d" % nL, np.linspace(1.8, 9.0, 41), 24, L, theta, wl.POISSON)
+    check_chain(api, Case(w), prec, mapping)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
 def test_points_sharing_grids(api, prec):
     # points with equal node counts share one energy grid on the device; the

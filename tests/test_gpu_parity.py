@@ -338,6 +338,22 @@ def test_baseline_counts_between_instantiations(api, nL, prec, mapping):
     check_chain(api, Case(w), prec, mapping)
 
 
+@pytest.mark.parametrize("prec,mapping", [("fp64", None), ("ff", "split"), ("ff", "bins"), ("ff", "slices")])
+def test_many_bins(api, prec, mapping):
+    # 40001 bins (1251 groups of 32, the last holding one bin) of 3 nodes
+    theta = np.array([wl.TRUTH])
+    w = wl.Workload("many_bins", np.linspace(1.8, 12.0, 40002), 3, np.array([52.5, 1.5]), theta, wl.PEARSON)
+    check_chain(api, Case(w), prec, mapping)
+
+
+@pytest.mark.parametrize("prec,mapping", [("fp64", None), ("ff", "split"), ("ff", "slices"), ("f64phase", "slices")])
+def test_one_bin_of_many_nodes(api, prec, mapping):
+    # one bin (one lane of one group busy) of 16384 nodes, eight baselines:
+    # the slice mapping cuts it into its largest number of slices
+    w = wl.shrink(wl.reactor8_1000x16384(), nbins=1)
+    check_chain(api, Case(w), prec, mapping)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
 def test_points_sharing_grids(api, prec):
     # points with equal node counts share one energy grid on the device; the

@@ -269,6 +269,7 @@ def side_workloads(api, torch, device, args):
     ms = a0.elapsed_time(a1) / reps
     pts = w.points_per_eval()
     ops = sum(fp32_ops_per_node(1, True, False) * w.nbins * int(n) for n in w.node_counts)
+    check = {"scan": (w, N, data.cpu().numpy(), o["chi2"].cpu().numpy(), o["grad"].cpu().numpy())}
     out["scan_64x64_500bins"] = {"scans_per_s": 1e3 / ms, "ms_per_scan": ms, "chi2_grad_evals_per_s": w.npts * 1e3 / ms,
                                  "gpoints_per_s": pts / ms / 1e6, "points_per_scan": pts,
                                  "fp32_frac_of_issue_peak": ops / (ms * 1e-3) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
@@ -300,6 +301,7 @@ def side_workloads(api, torch, device, args):
     plan.status()
     ms = a0.elapsed_time(a1)
     pts = w.points_per_eval() * w.fit_iters
+    check["fits"] = (w, N, data[0].cpu().numpy(), p[0].cpu().numpy(), c2[0].item())
     out["fits_16384x1000"] = {"fits_per_s": w.npts * 1e3 / ms, "ms_per_batch": ms, "iterations": w.fit_iters,
                               "chi2_grad_evals_per_s": w.npts * w.fit_iters * 1e3 / ms, "gpoints_per_s": pts / ms / 1e6,
                               "median_best_chi2": float(c2.median()), "tuning": plan.tuning, "graph": True}
@@ -329,6 +331,56 @@ def side_workloads(api, torch, device, args):
         res[prec] = {"evals_per_s": 1e3 / ms, "us_per_eval": ms * 1e3, "tuning": plan.tuning}
         plan.close()
     out["reactor_200x50"] = dict(res, note="10^4 nodes: launch-latency bound (graph replay of 2-3 kernels)")
+    # differentiable chi2 with 1000 per-bin nuisances (1000 bins x 4096 nodes x
+    # 8 baselines): chi2 and its hand-written adjoint d chi2 / d(theta, eta)
+    # through the autograd Function (forward + backward), and the same
+    # evaluation called directly
+    w = wl.nuisance_1000x4096()
+    plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, norm=1.0, prec=args.prec, kind=w.kind)
+    truth = plan.params_tensor(w.truth)
+    m = plan.eval(truth, torch.ones(w.nbins, dtype=torch.float64, device=device), grad=False, mu=True)["mu"][0]
+    N = wl.TOTAL_EVENTS / float(m.sum())
+    plan.close()
+    plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, norm=N, prec=args.prec, kind=w.kind)
+    data = torch.as_tensor(wl.poisson_data((m * N).cpu().numpy(), w.data_seed), device=device)
+    plan.autotune(plan.params_tensor(w.theta), data, reps=5, grad=True)
+    theta = torch.tensor(w.theta[0], dtype=torch.float64, device=device, requires_grad=True)
+    eta = torch.tensor(w.eta, dtype=torch.float64, device=device, requires_grad=True)
+
+    def ad_step():
+        theta.grad = None
+        eta.grad = None
+        api.chi2(theta, plan, data, eta, w.sigma_eta).backward()
+
+    pt, et = plan.params_tensor(w.theta), torch.as_tensor(w.eta, device=device)
+    od = {"chi2": torch.empty(1, dtype=torch.float64, device=device),
+          "grad": torch.empty(1, 4, dtype=torch.float64, device=device),
+          "grad_eta": torch.empty(1, w.nbins, dtype=torch.float64, device=device)}
+
+    def direct_step():
+        plan.eval(pt, data, et, w.sigma_eta, grad=True, grad_eta=True, out=od)
+
+    res = {}
+    for name, fn in (("autograd", ad_step), ("direct", direct_step)):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        for _ in range(100):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a0.elapsed_time(a1) / 100 * 1e3
+    check["nuisance"] = (w, N, data.cpu().numpy(), od["chi2"][0].item(), od["grad"][0].cpu().numpy(),
+                         od["grad_eta"][0].cpu().numpy())
+    ops = fp32_ops_per_node(w.nL, True, False) * w.nbins * w.nodes_per_bin
+    out["nuisance_1000x4096"] = {
+        "evals_per_s_autograd": 1e6 / res["autograd"], "us_per_eval_autograd": res["autograd"],
+        "us_per_eval_direct": res["direct"], "gpoints_per_s": w.points_per_eval() / res["direct"] / 1e3,
+        "fp32_frac_of_issue_peak": ops / (res["direct"] * 1e-6) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
+        "outputs": "chi2, d chi2 / d(4 oscillation parameters, 1000 nuisances)", "tuning": plan.tuning}
+    plan.close()
     # the paper's Table 1 shape: bare OscProb in FP64 on 10^4 and 10^6 energies,
     # GPU compute only and with the host<->device transfers (the host side is
     # timed in the CPU-baseline leg)
@@ -412,7 +464,34 @@ def side_workloads(api, torch, device, args):
     ms = a0.elapsed_time(a1) / 5
     out["pseudo_data_16384x1000"] = {"ms": ms, "gsamples_per_s": wf.npts * wf.nbins / (ms * 1e-3) / 1e9,
                                      "mu_range": [20.0, 400.0]}
-    return out
+    return out, check
+
+
+def cpu_side_errors(side, check):
+    """CPU-baseline leg of the batched workloads: the oracle at sampled points
+    of the scan, on the nuisance evaluation and on one fit; adds each
+    workload's error against it."""
+    import oracle
+
+    rmax = lambda a, b: float(np.max(np.abs(np.asarray(a) - b) / np.abs(b)))
+    nrel = lambda a, b: float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+    w, N, d, c2, g = check["scan"]
+    e = {"points": [0, 2049, 4095], "chi2": 0.0, "grad_normwise": 0.0}
+    for p in e["points"]:
+        r = oracle.chain(w.edges, int(w.node_counts[p]), w.L, w.theta[p], N, d, w.kind, e_scale=w.e_scale)
+        e["chi2"] = max(e["chi2"], rmax(c2[p], r["chi2"]))
+        e["grad_normwise"] = max(e["grad_normwise"], nrel(g[p], r["grad"][:4]))
+    side["scan_64x64_500bins"]["error_vs_oracle"] = e
+    w, N, d, c2, g, ge = check["nuisance"]
+    r = oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], N, d, w.kind, eta=w.eta, sigma=w.sigma_eta)
+    side["nuisance_1000x4096"]["error_vs_oracle"] = {
+        "chi2": rmax(c2, r["chi2"]), "grad_normwise": nrel(g, r["grad"][:4]),
+        "grad_eta_normwise": nrel(ge, r["grad"][4:])}
+    w, N, d, pf, c2 = check["fits"]
+    ev = lambda t: oracle.chain(w.edges, w.nodes_per_bin, w.L, t, N, d, w.kind)
+    th, c2o, _ = oracle.fit_lm(ev, w.theta[0], iters=w.fit_iters)
+    side["fits_16384x1000"]["error_vs_oracle"] = {
+        "dataset": 0, "best_chi2": rmax(c2, c2o), "best_params": rmax(pf, th)}
 
 
 def cpu_oscprob_table1(t1):
@@ -638,9 +717,10 @@ def main():
             "spectra": rmax(go["spectra"][0].cpu().numpy(), ref["mu_rb"]),
             "grad_normwise": float(np.linalg.norm(g - ref["grad"][:4]) / np.linalg.norm(ref["grad"][:4]))}
 
-    side = None if args.no_side else side_workloads(api, torch, device, args)
+    side, check = (None, None) if args.no_side else side_workloads(api, torch, device, args)
     if side is not None and cpu is not None:
         cpu_oscprob_table1(side["oscprob_fp64_table1_shape"])
+        cpu_side_errors(side, check)
 
     if rank == 0:
         line = {"metric": METRIC, "value": evals_per_s, "unit": "evals/s", "n_gpus": world, "steps": args.steps,

@@ -447,15 +447,25 @@ class OscChi2(torch.autograd.Function):
             raise ValueError("OscChi2 works on a single-point plan")
         p = theta.detach().reshape(1, 4).contiguous()
         e = None if eta is None else eta.detach().contiguous()
-        r = plan.eval(p, data, e, sigma, grad=True, grad_eta=e is not None)
-        ctx.save_for_backward(r["grad"][0].clone(), r["grad_eta"][0].clone() if e is not None else torch.zeros(0))
+        # the library writes chi2 and the whole gradient [4 (+ nbins)] straight
+        # into the tensors this call returns and keeps (no copies)
+        chi2 = torch.empty((), dtype=torch.float64, device=p.device)
+        g = torch.empty(4 + (plan.nbins if e is not None else 0), dtype=torch.float64, device=p.device)
+        out = {"chi2": chi2, "grad": g[:4]}
+        if e is not None:
+            out["grad_eta"] = g[4:]
+        plan.eval(p, data, e, sigma, grad=True, grad_eta=e is not None, out=out)
+        ctx.save_for_backward(g)
         ctx.has_eta = e is not None
-        return r["chi2"][0].clone()
+        ctx.shapes = (theta.shape, None if eta is None else eta.shape)
+        return chi2
 
     @staticmethod
-    def backward(ctx, g):
-        gt, ge = ctx.saved_tensors
-        return g * gt, (g * ge if ctx.has_eta else None), None, None, None
+    def backward(ctx, go):
+        (g,) = ctx.saved_tensors
+        h = go * g
+        ts, es = ctx.shapes
+        return h[:4].view(ts), (h[4:].view(es) if ctx.has_eta else None), None, None, None
 
 
 def chi2(theta, plan: Plan, data, eta=None, sigma: float = 0.0):

@@ -555,6 +555,16 @@ def test_autograd_function(api):
     g_fd = oracle.fd_grad(f, w.theta[0])
     assert normrel(ref["grad"][:4], g_fd) < 1e-5
 
+    # a [1, 4] parameter tensor and no nuisances; results of successive calls
+    # are independent tensors
+    th2 = dev(w.theta[0]).reshape(1, 4).requires_grad_(True)
+    c1 = api.chi2(th2, plan, d)
+    c2 = api.chi2(dev(w.theta[0] * 1.01), plan, d)
+    c1.backward()
+    ref0 = oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], case.N, case.data, w.kind)
+    assert c1.dim() == 0 and rel(c1.item(), ref0["chi2"]) < 1e-9 and c2.item() != c1.item()
+    assert tuple(th2.grad.shape) == (1, 4) and normrel(th2.grad[0].cpu().numpy(), ref0["grad"][:4]) < 1e-9
+
 
 @pytest.mark.parametrize("prec", ["fp64", "ff"])
 def test_fits_match_oracle(api, prec):

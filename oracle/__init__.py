@@ -66,6 +66,9 @@ def _configure(lib):
     lib.or_binned.restype = _I
     lib.or_chi2.argtypes = [_I, _I, _PD, _PD, _PD, _D, _PD, _D, _PD, _I, _PD, _PD, _PD]
     lib.or_chi2.restype = _D
+    lib.or_prob_grad.argtypes = [_I, _I, _PD, _D, _D, _I, _PD, _PD]
+    lib.or_binned_general.argtypes = [_I, _PD, _I, _PD, _PD, _I, _PD, _PD, _I, _I, _I, _D, _PD, _PD]
+    lib.or_binned_general.restype = _I
     _PU = ctypes.POINTER(ctypes.c_uint32)
     lib.or_philox4x32_10.argtypes = [_PU, _PU, _PU]
     lib.or_poisson_inv.argtypes = [_D, _D, _D]
@@ -228,6 +231,70 @@ def chain(edges, n, L_km, osc, N, data, kind=0, eta=None, sigma=0.0, e_scale=1.0
     out["dmu_rb"] = dmu_rb
     out["omega"] = om
     return out
+
+
+FLAVOUR = {"e": 0, "mu": 1, "tau": 2}
+
+
+def prob_grad(alpha, beta, osc6, L_km, E_MeV, anti=False):
+    """P(alpha -> beta) and dP / d(s12^2, s13^2, s23^2, delta, dm2_21, dm2_32) at one
+    energy, from the Sec. 4.1 formula and the product rule on the mixing matrix."""
+    P = ctypes.c_double()
+    dP = np.empty(6)
+    _load().or_prob_grad(FLAVOUR.get(alpha, alpha), FLAVOUR.get(beta, beta), _p(_f64(osc6)), float(L_km),
+                         float(E_MeV), int(bool(anti)), ctypes.byref(P), _p(dP))
+    return P.value, dP
+
+
+def binned_general(edges, n, L_km, osc6, alpha, beta, anti=False, e_scale=1.0):
+    """Per-baseline binned prediction of P(alpha -> beta): mu[nL][nbins] and
+    d mu / d(six parameters) [nL][nbins][6]."""
+    edges = _f64(edges)
+    L = _f64(np.atleast_1d(L_km))
+    nb = edges.size - 1
+    x, w = _gl_cached(int(n))
+    mu = np.empty((L.size, nb))
+    dmu = np.empty((L.size, nb, 6))
+    _load().or_binned_general(nb, _p(edges), int(n), _p(x), _p(w), L.size, _p(L), _p(_f64(osc6)),
+                              FLAVOUR.get(alpha, alpha), FLAVOUR.get(beta, beta), int(bool(anti)),
+                              float(e_scale), _p(mu), _p(dmu))
+    return mu, dmu
+
+
+def chain_general(edges, n, L_km, osc6, N, data, alpha, beta, anti=False, kind=0, eta=None, sigma=0.0,
+                  e_scale=1.0, omega=None):
+    """One evaluation of the chain for P(alpha -> beta) at one point of the six
+    parameters.  The detector combination and chi^2 are the textbook ones of
+    ``chi2`` (M_i = sum_r omega_r mu[r][i], mu_i = N (1 + eta_i) M_i, Pearson or
+    Poisson, the nuisance penalty), written out here for six parameters.
+    Returns dict(chi2, grad[6 + nbins], mu[nbins], mu_rb, dmu_rb)."""
+    L = np.atleast_1d(_f64(L_km))
+    om = baseline_weights(L) if omega is None else _f64(omega)
+    mu_rb, dmu_rb = binned_general(edges, n, L, osc6, alpha, beta, anti, e_scale)
+    d = _f64(data)
+    nb = d.size
+    e = np.zeros(nb) if eta is None else _f64(eta)
+    chi2v = 0.0
+    grad = np.zeros(6 + nb)
+    mu = np.empty(nb)
+    for i in range(nb):
+        M = sum(om[r] * mu_rb[r, i] for r in range(L.size))
+        dM = sum(om[r] * dmu_rb[r, i] for r in range(L.size))
+        m = N * (1.0 + e[i]) * M
+        if kind == 0:
+            term = (d[i] - m) ** 2 / m
+            gi = 1.0 - d[i] * d[i] / (m * m)
+        else:
+            term = 2.0 * (m - d[i] + d[i] * np.log(d[i] / m)) if d[i] > 0 else 2.0 * m
+            gi = 2.0 * (1.0 - d[i] / m)
+        chi2v += term
+        mu[i] = m
+        grad[:6] += gi * N * (1.0 + e[i]) * dM
+        grad[6 + i] = gi * N * M
+        if eta is not None and sigma > 0:
+            chi2v += e[i] * e[i] / (sigma * sigma)
+            grad[6 + i] += 2.0 * e[i] / (sigma * sigma)
+    return {"chi2": chi2v, "grad": grad, "mu": mu, "mu_rb": mu_rb, "dmu_rb": dmu_rb, "omega": om}
 
 
 def norm_for_total(edges, n, L_km, osc, total=1e5, e_scale=1.0, omega=None) -> float:

@@ -278,6 +278,120 @@ int or_binned(int nbins, const double* edges, int n, const double* x, const doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Any channel with its gradient (beyond the nue_bar survival chain).        */
+/* dU/dp for p = (s12^2, s13^2, s23^2, delta): the product rule on           */
+/* U = R23 U13(delta) R12, each rotation differentiated in its own variable   */
+/* (d sin(theta)/d sin^2(theta) = 1 / (2 sin(theta)), d cos(theta) /          */
+/* d sin^2(theta) = -1 / (2 cos(theta)); d e^(-+i delta)/d delta = -+i        */
+/* e^(-+i delta)).  Interior points only (0 < s^2 < 1).                      */
+/* ------------------------------------------------------------------------ */
+static void pmns_dU(double s12sq, double s13sq, double s23sq, double delta,
+                    double complex dU[4][3][3]) {
+    double s12 = sqrt(s12sq), c12 = sqrt(1.0 - s12sq);
+    double s13 = sqrt(s13sq), c13 = sqrt(1.0 - s13sq);
+    double s23 = sqrt(s23sq), c23 = sqrt(1.0 - s23sq);
+    double complex em = cexp(-I * delta), ep = cexp(I * delta);
+    double complex R23[3][3] = {{1, 0, 0}, {0, c23, s23}, {0, -s23, c23}};
+    double complex R13[3][3] = {{c13, 0, s13 * em}, {0, 1, 0}, {-s13 * ep, 0, c13}};
+    double complex R12[3][3] = {{c12, s12, 0}, {-s12, c12, 0}, {0, 0, 1}};
+    double ds12 = 0.5 / s12, dc12 = -0.5 / c12;
+    double ds13 = 0.5 / s13, dc13 = -0.5 / c13;
+    double ds23 = 0.5 / s23, dc23 = -0.5 / c23;
+    double complex D12[3][3] = {{dc12, ds12, 0}, {-ds12, dc12, 0}, {0, 0, 0}};
+    double complex D13[3][3] = {{dc13, 0, ds13 * em}, {0, 0, 0}, {-ds13 * ep, 0, dc13}};
+    double complex D23[3][3] = {{0, 0, 0}, {0, dc23, ds23}, {0, -ds23, dc23}};
+    double complex Dd[3][3] = {{0, 0, -I * s13 * em}, {0, 0, 0}, {-I * s13 * ep, 0, 0}};
+    double complex T[3][3];
+    mat3_mul(R23, R13, T);
+    mat3_mul(T, D12, dU[0]);
+    mat3_mul(R23, D13, T);
+    mat3_mul(T, R12, dU[1]);
+    mat3_mul(D23, R13, T);
+    mat3_mul(T, R12, dU[2]);
+    mat3_mul(R23, Dd, T);
+    mat3_mul(T, R12, dU[3]);
+}
+
+/* P(a->b) of the Sec. 4.1 formula (as prob_general) and its derivatives     */
+/* dP[6] with respect to (s12^2, s13^2, s23^2, delta, dm2_21, dm2_32):        */
+/* for the mixing parameters the product rule on X_ij = V*_ai V_bi V_aj V*_bj */
+/* with dV = dU (or its conjugate for antineutrinos); for the mass           */
+/* splittings d/dx [-4 Re X sin^2 x + 2 Im X sin 2x] = -4 Re X sin 2x +      */
+/* 4 Im X cos 2x times dx/d(dm2).                                             */
+static void prob_general_grad(int a, int b, const double complex U[3][3],
+                              const double complex dU[4][3][3], double dm21, double dm32,
+                              double L_km, double E_MeV, int anti, double* P, double* dP) {
+    double complex V[3][3], dV[4][3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            V[r][c] = anti ? conj(U[r][c]) : U[r][c];
+            for (int q = 0; q < 4; q++) dV[q][r][c] = anti ? conj(dU[q][r][c]) : dU[q][r][c];
+        }
+    double m2[3] = {0.0, dm21, dm21 + dm32};
+    double dm2_d21[3] = {0.0, 1.0, 1.0};
+    double dm2_d32[3] = {0.0, 0.0, 1.0};
+    double p = (a == b) ? 1.0 : 0.0;
+    for (int q = 0; q < 6; q++) dP[q] = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < i; j++) {
+            double complex X = conj(V[a][i]) * V[b][i] * V[a][j] * conj(V[b][j]);
+            double x = half_phase(m2[i] - m2[j], L_km, E_MeV);
+            double sx = sin(x), s2x = sin(2.0 * x), c2x = cos(2.0 * x);
+            p += -4.0 * creal(X) * sx * sx + 2.0 * cimag(X) * s2x;
+            for (int q = 0; q < 4; q++) {
+                double complex dX = conj(dV[q][a][i]) * V[b][i] * V[a][j] * conj(V[b][j]) +
+                                    conj(V[a][i]) * dV[q][b][i] * V[a][j] * conj(V[b][j]) +
+                                    conj(V[a][i]) * V[b][i] * dV[q][a][j] * conj(V[b][j]) +
+                                    conj(V[a][i]) * V[b][i] * V[a][j] * conj(dV[q][b][j]);
+                dP[q] += -4.0 * creal(dX) * sx * sx + 2.0 * cimag(dX) * s2x;
+            }
+            double dterm_dx = -4.0 * creal(X) * s2x + 4.0 * cimag(X) * c2x;
+            double dx = half_phase(1.0, L_km, E_MeV);
+            dP[4] += dterm_dx * dx * (dm2_d21[i] - dm2_d21[j]);
+            dP[5] += dterm_dx * dx * (dm2_d32[i] - dm2_d32[j]);
+        }
+    *P = p;
+}
+
+/* osc6 = (s12^2, s13^2, s23^2, delta, dm2_21, dm2_32); dP[6] as above.      */
+void or_prob_grad(int alpha, int beta, const double* osc6, double L_km, double E_MeV, int anti,
+                  double* P, double* dP) {
+    double complex U[3][3], dU[4][3][3];
+    pmns_complex(osc6[0], osc6[1], osc6[2], osc6[3], U);
+    pmns_dU(osc6[0], osc6[1], osc6[2], osc6[3], dU);
+    prob_general_grad(alpha, beta, U, dU, osc6[4], osc6[5], L_km, E_MeV, anti, P, dP);
+}
+
+/* Binned prediction per baseline for P(alpha -> beta), as or_binned, with   */
+/* dmu[r][i][6] (optional) the derivatives in the six parameters above.      */
+int or_binned_general(int nbins, const double* edges, int n, const double* x, const double* w,
+                      int nL, const double* L_km, const double* osc6, int alpha, int beta, int anti,
+                      double e_scale, double* mu, double* dmu) {
+    double complex U[3][3], dU[4][3][3];
+    pmns_complex(osc6[0], osc6[1], osc6[2], osc6[3], U);
+    pmns_dU(osc6[0], osc6[1], osc6[2], osc6[3], dU);
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (int r = 0; r < nL; r++)
+        for (int i = 0; i < nbins; i++) {
+            double a = edges[i], b = edges[i + 1];
+            double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+            double s = 0, g[6] = {0, 0, 0, 0, 0, 0};
+            for (int k = 0; k < n; k++) {
+                double E = mid + half * x[k];
+                double wt = half * w[k] * or_spectrum(E, e_scale);
+                double P, dP[6];
+                prob_general_grad(alpha, beta, U, dU, osc6[4], osc6[5], L_km[r], E, anti, &P, dP);
+                s += wt * P;
+                for (int q = 0; q < 6; q++) g[q] += wt * dP[q];
+            }
+            mu[(int64_t)r * nbins + i] = s;
+            if (dmu)
+                for (int q = 0; q < 6; q++) dmu[((int64_t)r * nbins + i) * 6 + q] = g[q];
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Detector prediction, chi^2 and gradient (not in the paper; textbook).     */
 /*   M_i  = sum_r omega_r mu[r][i]                    (baseline combination) */
 /*   mu_i = N (1 + eta_i) M_i                          (normalisation, nuis.) */

@@ -38,6 +38,15 @@ MUTATIONS = {
                                "g12 -= 4.0 * (due_ds12[i] * ue[j]) * s2;"),
     "grad_dm21_chain": ("double dm2_d21[3] = {0.0, 1.0, 1.0};", "double dm2_d21[3] = {0.0, 1.0, 0.0};"),
     "penalty_sigma": ("chi2 += eta[i] * eta[i] / (sigma * sigma);", "chi2 += eta[i] * eta[i] / sigma;"),
+    "dU_delta_sign": ("double complex Dd[3][3] = {{0, 0, -I * s13 * em}", "double complex Dd[3][3] = {{0, 0, I * s13 * em}"),
+    "dU_not_conjugated_for_antineutrinos": ("dV[q][r][c] = anti ? conj(dU[q][r][c]) : dU[q][r][c];",
+                                            "dV[q][r][c] = dU[q][r][c];"),
+    "dU_s23_cos_sign": ("double ds23 = 0.5 / s23, dc23 = -0.5 / c23;", "double ds23 = 0.5 / s23, dc23 = 0.5 / c23;"),
+    "general_grad_product_rule_term": ("conj(V[a][i]) * V[b][i] * dV[q][a][j] * conj(V[b][j]) +\n", ""),
+    "general_grad_im_term_dm": ("double dterm_dx = -4.0 * creal(X) * s2x + 4.0 * cimag(X) * c2x;",
+                                "double dterm_dx = -4.0 * creal(X) * s2x + 2.0 * cimag(X) * c2x;"),
+    "general_grad_dm32_chain": ("dP[5] += dterm_dx * dx * (dm2_d32[i] - dm2_d32[j]);",
+                                "dP[5] += dterm_dx * dx * (dm2_d21[i] - dm2_d21[j]);"),
 }
 
 

@@ -397,3 +397,82 @@ def test_lm_fit_recovers_truth_on_asimov_data():
     assert hist.size == 20
     assert c2 < 1e-8
     assert np.abs(th / np.array(TRUTH) - 1).max() < 1e-4
+
+
+# ------------------------------------------------- any channel, gradient ----
+TH6 = (0.307, 0.0218, 0.545, 1.2 * np.pi, 7.53e-5, 2.44e-3)
+
+
+def fd6(f, th, rel_h=1e-6):
+    g = np.empty(6)
+    for q in range(6):
+        h = rel_h * abs(th[q])
+        tp, tm = list(th), list(th)
+        tp[q] += h
+        tm[q] -= h
+        g[q] = (f(tp) - f(tm)) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("a,b,anti,L,E", [("mu", "e", False, 810.0, 2000.0), ("mu", "mu", True, 810.0, 1500.0),
+                                          ("e", "tau", False, 295.0, 600.0), ("tau", "mu", True, 1300.0, 3100.0),
+                                          ("e", "e", True, 52.5, 4.0)])
+def test_general_gradient_matches_central_differences(a, b, anti, L, E):
+    # the analytic derivative of the Sec. 4.1 formula against differences of the
+    # formula itself, in all six parameters
+    P, dP = oracle.prob_grad(a, b, TH6, L, E, anti)
+    fa, fb = oracle.FLAVOUR[a], oracle.FLAVOUR[b]
+    assert P == oracle.prob(fa, fb, *TH6, L, E, anti)
+    g = fd6(lambda t: oracle.prob(fa, fb, *t, L, E, anti), TH6)
+    assert np.linalg.norm(dP - g) <= 1e-6 * np.linalg.norm(g)
+
+
+def test_general_gradient_unitarity_and_cpt():
+    # sum over final (or initial) flavours of P is 1 for any parameters, so the
+    # derivatives sum to zero; CPT maps nu_bar a->b to nu b->a, derivatives too
+    fl = ["e", "mu", "tau"]
+    for E in (700.0, 2500.0):
+        for a in fl:
+            assert np.abs(sum(oracle.prob_grad(a, b, TH6, 810.0, E)[1] for b in fl)).max() < 1e-12 * 1e3
+            assert np.abs(sum(oracle.prob_grad(b, a, TH6, 810.0, E, True)[1] for b in fl)).max() < 1e-12 * 1e3
+            for b in fl:
+                P1, d1 = oracle.prob_grad(a, b, TH6, 810.0, E, True)
+                P2, d2 = oracle.prob_grad(b, a, TH6, 810.0, E, False)
+                assert abs(P1 - P2) < 1e-14 and np.abs(d1 - d2).max() < 1e-10
+
+
+def test_general_ee_gradient_is_the_closed_form():
+    # for nue_bar survival the derivative in (s12^2, s13^2, dm21, dm32) equals
+    # the closed-form moduli product rule, and theta23 and delta do not enter
+    E = np.linspace(1.8, 12.0, 7)
+    osc = (TH6[0], TH6[1], TH6[4], TH6[5])
+    P, dP = oracle.pee_grad(E, 52.5, osc)
+    for k, e in enumerate(E):
+        p, d = oracle.prob_grad("e", "e", TH6, 52.5, e, True)
+        assert abs(p - P[k]) < 1e-14
+        assert np.abs(d[[0, 1, 4, 5]] - dP[k]).max() <= 1e-12 * (1 + np.abs(dP[k]).max())
+        assert abs(d[2]) < 1e-13 and abs(d[3]) < 1e-13
+
+
+def test_general_chain_reduces_to_the_ee_chain_and_matches_differences():
+    edges = np.linspace(1.8, 9.0, 13)
+    L = np.array([52.5, 20.0])
+    n = 12
+    osc = (TH6[0], TH6[1], TH6[4], TH6[5])
+    N = oracle.norm_for_total(edges, n, L, osc)
+    data = wl.poisson_data(N * (oracle.baseline_weights(L) @ oracle.binned(edges, n, L, osc)), 5)
+    eta = np.random.default_rng(3).normal(0, 0.02, 12)
+    g = oracle.chain_general(edges, n, L, TH6, N, data, "e", "e", True, 1, eta, 0.02)
+    r = oracle.chain(edges, n, L, osc, N, data, 1, eta=eta, sigma=0.02)
+    assert abs(g["chi2"] - r["chi2"]) <= 1e-12 * r["chi2"]
+    assert np.abs(g["mu"] / r["mu"] - 1).max() < 1e-13
+    assert np.linalg.norm(g["grad"][[0, 1, 4, 5]] - r["grad"][:4]) <= 1e-10 * np.linalg.norm(r["grad"][:4])
+    assert np.abs(g["grad"][6:] - r["grad"][4:]).max() <= 1e-10 * np.abs(r["grad"][4:]).max()
+    # numu -> nue at 810 km: the chi^2 gradient against central differences
+    e2 = np.linspace(500.0, 5000.0, 11)
+    N2 = 1e4
+    d2 = wl.poisson_data(N2 * oracle.binned_general(e2, 10, [810.0], TH6, "mu", "e", e_scale=1e-3)[0][0], 6)
+    th = (0.31, 0.0225, 0.52, 1.4 * np.pi, 7.4e-5, 2.5e-3)
+    f = lambda t: oracle.chain_general(e2, 10, [810.0], t, N2, d2, "mu", "e", kind=1, e_scale=1e-3)["chi2"]
+    gr = oracle.chain_general(e2, 10, [810.0], th, N2, d2, "mu", "e", kind=1, e_scale=1e-3)["grad"][:6]
+    assert np.linalg.norm(gr - fd6(f, th)) <= 1e-5 * np.linalg.norm(gr)

@@ -85,6 +85,8 @@ typedef struct {
     gna_chi2_kind kind;
     int max_datasets;           /* >= npts when each point has its own data row (fits); 0 = npts */
     int flags;                  /* GNA_PLAN_* bits below */
+    int alpha, beta;            /* with GNA_PLAN_GENERAL: the channel P(alpha -> beta), 0 = e, 1 = mu, 2 = tau */
+    int anti;                   /* with GNA_PLAN_GENERAL: 1 for antineutrinos, 0 for neutrinos */
 } gna_plan_desc;
 
 #define GNA_PLAN_WITH_PLAIN 1  /* also build the FP64 arrays and scratch of gna_chain_eval_plain */
@@ -93,6 +95,10 @@ typedef struct {
 #define GNA_PLAN_FORCE_SLICES 8 /* one thread per bin and slice of its nodes, slices summed by a
                                    second kernel (default for uniform grids in the mixed
                                    precisions when points x bin groups are too few to fill the GPU) */
+#define GNA_PLAN_GENERAL 16     /* the chain for any channel (alpha, beta, anti above), evaluated by
+                                   gna_chain_eval_general: mixed precisions, up to 8 baselines, the
+                                   slice mapping on equal node counts and the bin mapping otherwise;
+                                   the survival-chain calls return GNA_ESTATE on such a plan */
 
 /* Outputs of one evaluation (device pointers; any may be NULL except chi2). */
 typedef struct {
@@ -261,6 +267,27 @@ gna_status gna_plan_info(const gna_plan* plan, int64_t* nodes, int64_t* points_p
  */
 gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
                           const double* data, int data_per_point, const gna_outputs* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gna_chain_eval_general: the same chain for any channel P(alpha -> beta)
+ * of a plan created with GNA_PLAN_GENERAL (paper Sec. 4.1, the general
+ * formula with its Im term; neutrinos use U, antineutrinos U*).
+ *   params: device [npts] gna_osc_full (s2_12, s2_13, s2_23, delta_cp,
+ *           dm2_21, dm2_32); the mixing parameters must lie inside (0, 1)
+ *           (the gradient is singular on the boundary): a point outside is
+ *           reported by gna_plan_status as GNA_EINVAL
+ *   eta, sigma_eta, data, data_per_point: as for gna_chain_eval
+ *   out:    chi2 [npts]; grad [npts][6] = d chi2 / d(s2_12, s2_13, s2_23,
+ *           delta_cp, dm2_21, dm2_32) or NULL; grad_eta and mu as for
+ *           gna_chain_eval; spectra must be NULL (GNA_EINVAL)
+ * The node pass accumulates channel-free sums per bin (sin^2 and sin cos of
+ * the three phases, and their derivatives in the phases); the epilogue
+ * contracts them with the point's coefficients -4 Re X_ij, 4 Im X_ij and
+ * their derivatives, X_ij = V*_ai V_bi V_aj V*_bj.  Asynchronous on
+ * `stream`; GNA_ESTATE on a survival-chain plan.
+ */
+gna_status gna_chain_eval_general(gna_plan* plan, const gna_osc_full* params, const double* eta, double sigma_eta,
+                                  const double* data, int data_per_point, const gna_outputs* out, void* stream);
 
 /* gna_chain_eval_cached: the epilogue only (steps a7-a9: nuisance
  * normalisation, chi^2, gradient contraction) on the per-bin node sums that

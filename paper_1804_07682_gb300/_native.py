@@ -21,6 +21,7 @@ GNA_PLAN_WITH_PLAIN = 1
 GNA_PLAN_FORCE_SPLIT = 2
 GNA_PLAN_FORCE_BINS = 4
 GNA_PLAN_FORCE_SLICES = 8
+GNA_PLAN_GENERAL = 16
 
 
 class GnaOsc(ctypes.Structure):
@@ -48,6 +49,9 @@ class GnaPlanDesc(ctypes.Structure):
         ("kind", c_int),
         ("max_datasets", c_int),
         ("flags", c_int),
+        ("alpha", c_int),
+        ("beta", c_int),
+        ("anti", c_int),
     ]
 
 
@@ -75,6 +79,8 @@ SIGNATURES = {
     "gna_plan_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
     "gna_chain_eval": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, ctypes.POINTER(GnaOutputs),
                                c_void_p]),
+    "gna_chain_eval_general": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int,
+                                       ctypes.POINTER(GnaOutputs), c_void_p]),
     "gna_chain_eval_cached": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_int, ctypes.POINTER(GnaOutputs),
                                       c_void_p]),
     "gna_chain_eval_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_void_p, c_void_p,

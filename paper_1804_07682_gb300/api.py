@@ -173,7 +173,10 @@ class Plan:
 
     def __init__(self, edges, L, nodes_per_bin: int = 0, npts: int = 1, node_counts=None, Lweight=None,
                  norm: float = 1.0, e_scale: float = 1.0, prec: str = "ff", kind="pearson", max_datasets: int = 0,
-                 with_plain: bool = False, mapping: Optional[str] = None, stream=None):
+                 with_plain: bool = False, mapping: Optional[str] = None, channel=None, stream=None):
+        """channel: None for the nue_bar survival chain (``eval``), or (alpha, beta,
+        anti) with flavours "e", "mu", "tau" for the chain of P(alpha -> beta)
+        (``eval_general``, parameters (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32))."""
         _require_cuda()
         self._lib = N.lib()
         self._edges = _f64(edges)
@@ -193,6 +196,11 @@ class Plan:
             flags |= N.GNA_PLAN_FORCE_SLICES
         elif mapping is not None:
             raise ValueError("mapping must be 'split', 'bins', 'slices' or None")
+        self.channel = None
+        if channel is not None:
+            a, b, anti = channel
+            self.channel = (FLAVOURS[a], FLAVOURS[b], int(bool(anti)))
+            flags |= N.GNA_PLAN_GENERAL
         P = ctypes.POINTER(ctypes.c_double)
         d = N.GnaPlanDesc()
         d.nbins = self.nbins
@@ -209,6 +217,8 @@ class Plan:
         d.kind = KINDS[kind]
         d.max_datasets = int(max_datasets)
         d.flags = flags
+        if self.channel is not None:
+            d.alpha, d.beta, d.anti = self.channel
         h = ctypes.c_void_p()
         code = self._lib.gna_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(_stream(stream)))
         N.check(code, what="gna_plan_create")
@@ -269,7 +279,8 @@ class Plan:
 
     # ------------------------------------------------------- evaluation --
     def params_tensor(self, theta) -> torch.Tensor:
-        t = torch.as_tensor(np.asarray(theta, dtype=np.float64).reshape(-1, 4), device=self.device)
+        npar = 4 if self.channel is None else 6
+        t = torch.as_tensor(np.asarray(theta, dtype=np.float64).reshape(-1, npar), device=self.device)
         if t.shape[0] != self.npts:
             raise ValueError("expected %d parameter points" % self.npts)
         return t.contiguous()
@@ -304,6 +315,36 @@ class Plan:
         code = fn(self._h, _ptr(params), _ptr(eta), float(sigma), _ptr(data), dpp, ctypes.byref(o),
                   ctypes.c_void_p(_stream(stream)))
         self._check(code, "gna_chain_eval_plain" if plain else "gna_chain_eval")
+        return out
+
+    def eval_general(self, params: torch.Tensor, data: torch.Tensor, eta: Optional[torch.Tensor] = None,
+                     sigma: float = 0.0, grad: bool = True, grad_eta: bool = False, mu: bool = False,
+                     out: Optional[dict] = None, stream=None) -> dict:
+        """One evaluation of all points of an any-channel plan.  params [npts, 6]
+        float64 CUDA (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32); data [nbins]
+        or [npts, nbins]; out["grad"] is [npts, 6]."""
+        if self.channel is None:
+            raise ValueError("the plan was created without a channel")
+        if params.dtype != torch.float64 or tuple(params.shape) != (self.npts, 6):
+            raise ValueError("params must be float64 [npts, 6]")
+        dpp = 1 if data.dim() == 2 else 0
+        if data.dtype != torch.float64 or data.shape[-1] != self.nbins or (dpp and data.shape[0] != self.npts):
+            raise ValueError("data must be float64 [nbins] or [npts, nbins]")
+        if eta is not None and (eta.dtype != torch.float64 or eta.numel() != self.nbins):
+            raise ValueError("eta must be float64 [nbins]")
+        if out is None:
+            out = {"chi2": self._out("chi2", (self.npts,))}
+            if grad:
+                out["grad"] = self._out("grad6", (self.npts, 6))
+            if grad_eta:
+                out["grad_eta"] = self._out("grad_eta", (self.npts, self.nbins))
+            if mu:
+                out["mu"] = self._out("mu", (self.npts, self.nbins))
+        o = N.GnaOutputs(_ptr(out["chi2"]), _ptr(out.get("grad")), _ptr(out.get("grad_eta")), _ptr(out.get("mu")),
+                         None)
+        code = self._lib.gna_chain_eval_general(self._h, _ptr(params), _ptr(eta), float(sigma), _ptr(data), dpp,
+                                                ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+        self._check(code, "gna_chain_eval_general")
         return out
 
     def eval_cached(self, data: torch.Tensor, eta: Optional[torch.Tensor] = None, sigma: float = 0.0,

@@ -1,0 +1,331 @@
+// general.cuh -- the chain for any channel P(alpha -> beta), neutrinos or
+// antineutrinos, with the gradient in the six parameters (s2_12, s2_13,
+// s2_23, delta_cp, dm2_21, dm2_32).
+//
+// Paper Sec. 4.1: P = delta_ab + sum_{i>j} [-4 Re X_ij sin^2 x_ij
+// + 2 Im X_ij sin 2x_ij], X_ij = V*_ai V_bi V_aj V*_bj.  Writing
+// a_ij = -4 Re X_ij, b_ij = 4 Im X_ij (sin 2x = 2 sin x cos x):
+//   P = delta_ab + sum_ij (a_ij S_ij + b_ij C_ij),  S = sin^2 x, C = sin x cos x.
+// The coefficients depend only on the mixing parameters and the channel, the
+// phases only on the mass splittings, so the node pass accumulates
+// channel-free sums and the epilogue contracts them with the point's
+// coefficients:
+//   U_ij = sum_k W_k sum_r omega_r S_ij,   V_ij = sum_k W_k sum_r omega_r C_ij,
+//   Y_ij = sum_k W_k/E_k sum_r w_r C_ij,   Z_ij = sum_k W_k/E_k sum_r w_r (cos^2 - sin^2)_ij,
+// w_r = 2 omega_r K L_r.  Then per bin
+//   M = delta_ab sum_k W_k + sum_ij (a_ij U_ij + b_ij V_ij),
+//   dM/dp = sum_ij (da_ij/dp U_ij + db_ij/dp V_ij) for the mixing parameters,
+//   dM/d dm2_21 = sum_{ij = 21, 31} (a_ij Y_ij + b_ij Z_ij / 2),
+//   dM/d dm2_32 = sum_{ij = 32, 31} (a_ij Y_ij + b_ij Z_ij / 2)
+// (d S / dx = 2 C, d C / dx = cos^2 - sin^2, dx/d dm2 = K L / E).
+// These kernels reuse the energy-grid layouts, the bin/slice task scheme and
+// the group and point reductions of the nue_bar survival chain; they are
+// separate kernels so that the survival chain's code stays as it is.
+#pragma once
+
+#include "epilogue.cuh"
+#include "fused.cuh"
+
+namespace gna {
+
+// Per-point coefficients of the general channel (prepared on the device).
+struct GenConst {
+    double dab;        // delta_ab
+    double a[3], b[3]; // pairs (21, 31, 32)
+    double da[4][3];   // d a / d(s2_12, s2_13, s2_23, delta)
+    double db[4][3];
+};
+
+struct GenArgs {
+    BinArgs b;
+    const GenConst* gc;  // [npts]
+};
+
+template <int PH, int NL, bool GRAD>
+struct NodeMathGen {
+    static constexpr int NV = GRAD ? 12 : 6;
+    // with several baselines the weights enter as hi + lo (no bias from the
+    // FP32 rounding of omega_r)
+    static constexpr bool LO = NL > 1;
+
+    PhaseConsts<PH, NL> ph;
+    float om[NL], omlo[NL], wkl[NL];
+
+    __device__ __forceinline__ void load(const PointConst* pc, const BaseConst& bc) {
+        ph.load(pc);
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            om[r] = bc.om[r];
+            omlo[r] = bc.omlo[r];
+            wkl[r] = bc.wkl[r];
+        }
+    }
+
+    // One energy node: g = {invE_hi, invE_lo, W, We}.
+    __device__ __forceinline__ void update(float4 g, KahanF (&acc)[NV]) const {
+        const float eh = g.x, el = g.y, W = g.z, We = g.w;
+        double ed = 0.0;
+        if (PH == 1) ed = (double)eh + (double)el;
+        float U[3] = {0.f, 0.f, 0.f}, V[3] = {0.f, 0.f, 0.f};
+        float Y[3] = {0.f, 0.f, 0.f}, Z[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            float s1, c1, s2, c2;
+            float r21, r32;
+            if (PH == 0) {
+                r21 = reduce_pi_ff(ph.ch21[r], ph.cl21[r], eh, el);
+                r32 = reduce_pi_ff(ph.ch32[r], ph.cl32[r], eh, el);
+            } else {
+                r21 = reduce_pi_f64(ph.cd21[r], ed);
+                r32 = reduce_pi_f64(ph.cd32[r], ed);
+            }
+            sincos_poly(r21, s1, c1);
+            sincos_poly(r32, s2, c2);
+            // x31 = x21 + x32 up to a multiple of pi: sin^2, sin cos and
+            // cos^2 - sin^2 do not see it
+            const float s3 = fmaf(s1, c2, c1 * s2);
+            const float c3 = fmaf(c1, c2, -(s1 * s2));
+            const float S[3] = {s1 * s1, s3 * s3, s2 * s2};
+            const float C[3] = {s1 * c1, s3 * c3, s2 * c2};
+            const float cc[3] = {c1, c3, c2};
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                U[j] = fmaf(om[r], S[j], U[j]);
+                V[j] = fmaf(om[r], C[j], V[j]);
+                if constexpr (LO) {
+                    U[j] = fmaf(omlo[r], S[j], U[j]);
+                    V[j] = fmaf(omlo[r], C[j], V[j]);
+                }
+                if constexpr (GRAD) {
+                    Y[j] = fmaf(wkl[r], C[j], Y[j]);
+                    Z[j] = fmaf(wkl[r], fmaf(cc[j], cc[j], -S[j]), Z[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            kadd_prod(acc[j], W, U[j]);
+            kadd_prod(acc[3 + j], W, V[j]);
+            if constexpr (GRAD) {
+                kadd_prod(acc[6 + j], We, Y[j]);
+                kadd_prod(acc[9 + j], We, Z[j]);
+            }
+        }
+    }
+};
+
+// Bin i of point p from its summed values v = [U(3), V(3)] (+ [Y(3), Z(3)])
+// and the point's coefficients: M and its six derivatives, then the chi^2
+// term and its gradient contributions into regs[0..6] (double-float pairs):
+// [0] the chi^2 term, [1 + q] g_i N (1 + eta_i) dM/dp_q.
+__device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int p, int i, const double* v,
+                                        const BinIn& in, float2* regs) {
+    const int64_t idx = (int64_t)p * a.nbins + i;
+    double M = c.dab * in.sumw;
+    for (int j = 0; j < 3; j++) M += c.a[j] * v[j] + c.b[j] * v[3 + j];
+    const double e = in.e;
+    const double f = a.norm * (1.0 + e);
+    const double mu = f * M;
+    const double d = in.d;
+    double term, gd;
+    if (a.kind == GNA_PEARSON) {
+        term = (d - mu) * (d - mu) / mu;
+        gd = 1.0 - (d * d) / (mu * mu);
+    } else {
+        term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
+        gd = 2.0 * (1.0 - d / mu);
+    }
+    const bool pen = a.eta && a.sigma > 0.0;
+    if (pen) term += e * e / (a.sigma * a.sigma);
+    regs[0] = to_ff(term);
+    if (a.has_grad) {
+        double dM[6];
+        for (int q = 0; q < 4; q++) {
+            dM[q] = 0.0;
+            for (int j = 0; j < 3; j++) dM[q] += c.da[q][j] * v[j] + c.db[q][j] * v[3 + j];
+        }
+        // pairs 0 = 21, 1 = 31, 2 = 32; x31 moves with both splittings
+        const double t31 = c.a[1] * v[7] + 0.5 * c.b[1] * v[10];
+        dM[4] = c.a[0] * v[6] + 0.5 * c.b[0] * v[9] + t31;
+        dM[5] = c.a[2] * v[8] + 0.5 * c.b[2] * v[11] + t31;
+        for (int q = 0; q < 6; q++) regs[1 + q] = to_ff(gd * f * dM[q]);
+    }
+    if (a.mu_out) a.mu_out[idx] = mu;
+    if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
+}
+
+// Point p: lane l sums groups l, l + 32, ... in order, then one transposed
+// reduction; chi2 and the six-parameter gradient are written.
+__device__ inline void gen_point_reduce(const EpiArgs& a, int p, int lane) {
+    float2 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = make_float2(0.f, 0.f);
+    for (int g = lane; g < a.ngroups; g += 32) {
+        const float2* gv = a.gvals + ((int64_t)p * a.ngroups + g) * a.NBV;
+#pragma unroll
+        for (int j = 0; j < 7; j++)
+            if (j < a.NBV) v[j] = ff_add(v[j], __ldcg(gv + j));
+    }
+    warp_transpose_reduce<16>(v, lane);
+    const int vi = lane >> 1;
+    if ((lane & 1) == 0 && vi < a.NBV) {
+        const double tot = (double)v[0].x + (double)v[0].y;
+        if (vi == 0) a.chi2[p] = tot;
+        else if (a.grad) a.grad[(int64_t)p * 6 + vi - 1] = tot;
+    }
+}
+
+// The group g of point p has its per-bin values in regs (whole warp calls):
+// sum the group, and the warp that completes the point's last group sums the
+// groups.
+static __device__ __noinline__ void gen_group_done(const EpiArgs& a, int p, int g, int lane, const float2* regs) {
+    group_reduce(a, p, g, lane, regs);
+    __threadfence();
+    __syncwarp();
+    int lastp = 0;
+    if (lane == 0) lastp = (atomicAdd(a.pt_cnt + p, 1) == a.ngroups - 1);
+    lastp = __shfl_sync(0xffffffffu, lastp, 0);
+    if (lastp) {
+        __threadfence();
+        gen_point_reduce(a, p, lane);
+    }
+}
+
+// Node kernel of the general channel, bin and slice mappings: the task scheme
+// and node loop of k_fused_bins with the channel-free sums above.
+template <int PH, int NL, bool GRAD>
+__global__ void __launch_bounds__(256) k_fused_bins_gen(GenArgs ga) {
+    using M = NodeMathGen<PH, NL, GRAD>;
+    constexpr int NV = M::NV;
+    const BinArgs& a = ga.b;
+    const int lane = threadIdx.x & 31;
+    int last_p = -1;
+    M m;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.ntasks) break;
+        int p, b, k0, n;
+        if (a.S > 1) {
+            const int per_point = a.ngroups * a.S;
+            p = t / per_point;
+            const int rem = t - p * per_point;
+            b = rem / a.S;
+            k0 = (rem - b * a.S) * a.L;
+            n = a.gn[0];
+        } else {
+            const int task = a.tasks[t];
+            p = task / a.ngroups;
+            b = task - p * a.ngroups;
+            k0 = 0;
+            n = a.gn[a.gid ? a.gid[p] : 0];
+        }
+        const int gi = a.gid ? a.gid[p] : 0;
+        const int kn = min(n, k0 + (a.S > 1 ? a.L : n)) - k0;
+        if (p != last_p) {
+            m.load(a.pcs + p, a.bc);
+            last_p = p;
+        }
+        KahanF acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) kzero(acc[v]);
+        const float4* g = a.grid + a.goff[gi] + ((int64_t)b * n + k0) * 32 + lane;
+        constexpr int D = (NL >= 4) ? 1 : 4;
+        float4 buf[D];
+#pragma unroll
+        for (int j = 0; j < D; j++) buf[j] = (j < kn) ? __ldg(g + (int64_t)j * 32) : make_float4(1.f, 0.f, 0.f, 0.f);
+        int k = 0;
+        for (; k + D <= kn; k += D) {
+#pragma unroll
+            for (int j = 0; j < D; j++) {
+                const float4 cur = buf[j];
+                const int kx = k + j + D;
+                buf[j] = (kx < kn) ? __ldg(g + (int64_t)kx * 32) : cur;
+                m.update(cur, acc);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; j++)
+            if (k + j < kn) m.update(buf[j], acc);
+        if (a.S > 1) {
+            float2* pp = a.part + (int64_t)t * NV * 32 + lane;
+#pragma unroll
+            for (int v = 0; v < NV; v++) pp[v * 32] = kahan_to_ff(acc[v]);
+            continue;
+        }
+        const int i = b * 32 + lane;
+        float2 regs[15];
+        if (i < a.nbins) {
+            double v[NV];
+#pragma unroll
+            for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
+            gen_bin_epilogue(a.ea, ga.gc[p], p, i, v, bin_inputs(a.ea, p, i), regs);
+        }
+        gen_group_done(a.ea, p, b, lane, regs);
+    }
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+// Slice sums of the general channel (NV <= 12 values), in slice order, then
+// the epilogue and the group and point reductions: k_slices_reduce with the
+// general epilogue.
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __restrict__ part, int S, int NV,
+                                                               EpiArgs ea, const GenConst* __restrict__ gc) {
+    constexpr int NVM = 12;
+    extern __shared__ float2 red[];  // [W][NV][32], then [NV][32] doubles
+    double* fin = reinterpret_cast<double*>(red + W * NV * 32);
+    const int pg = blockIdx.x;
+    const int p = pg / ea.ngroups;
+    const int g = pg - p * ea.ngroups;
+    const int w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    float2 acc[NVM];
+#pragma unroll
+    for (int v = 0; v < NVM; v++) acc[v] = make_float2(0.f, 0.f);
+    const int i = g * 32 + lane;
+    BinIn in{0.0, 0.0, 0.0};
+    if (w == 0 && i < ea.nbins) in = bin_inputs(ea, p, i);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const float2* base = part + (int64_t)pg * S * NV * 32 + lane;
+    const int64_t stride = (int64_t)NV * 32;
+    for (int sl = w; sl < S; sl += W) {
+        const float2* src = base + sl * stride;
+        float2 t[NVM];
+#pragma unroll
+        for (int v = 0; v < NVM; v++) t[v] = (v < NV) ? __ldg(src + v * 32) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < NVM; v++)
+            if (v < NV) acc[v] = ff_add(acc[v], t[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NVM; v++)
+        if (v < NV) red[(w * NV + v) * 32 + lane] = acc[v];
+    __syncthreads();
+    for (int v = w; v < NV; v += W) {
+        float2 sum = red[v * 32 + lane];
+        for (int k = 1; k < W; k++) sum = ff_add(sum, red[(k * NV + v) * 32 + lane]);
+        fin[v * 32 + lane] = (double)sum.x + (double)sum.y;
+    }
+    __syncthreads();
+    if (w == 0) {
+        double vals[NVM];
+        for (int v = 0; v < NV; v++) vals[v] = fin[v * 32 + lane];
+        float2 regs[15];
+        if (i < ea.nbins) gen_bin_epilogue(ea, gc[p], p, i, vals, in, regs);
+        gen_group_done(ea, p, g, lane, regs);
+    }
+}
+
+// Launchers (general.cu).
+cudaError_t launch_prepare_general(const gna_osc_full* prm, int npts, const BaseConst& bc, int alpha, int beta,
+                                   int anti, PointConst* out, GenConst* gout, int* zero, int64_t nz, int* status,
+                                   cudaStream_t s);
+cudaError_t dispatch_general(int ph, int nl, bool grad, const GenArgs& a, int grid, int block, cudaStream_t s);
+int general_resident_ctas(int ph, int nl, bool grad, int block);
+cudaError_t launch_slices_reduce_general(const float2* part, int S, int NV, const EpiArgs& ea, const GenConst* gc,
+                                         int npts, cudaStream_t s);
+
+}  // namespace gna

@@ -20,6 +20,7 @@
 #include "dispatch.h"
 #include "fused.cuh"
 #include "fused64.cuh"
+#include "general.cuh"
 #include "gnaosc.h"
 #include "misc.h"
 
@@ -90,6 +91,11 @@ struct gna_plan {
     int prec = GNA_MIXED_FFPHASE, kind = GNA_PEARSON, flags = 0, max_datasets = 0;
     int mapping = MAP_SPLIT;
     int sm_count = 0;
+    // any-channel plans (GNA_PLAN_GENERAL): P(g_alpha -> g_beta), antineutrinos
+    // when g_anti; their coefficients are prepared per point into d_gc
+    bool general = false;
+    int g_alpha = 0, g_beta = 0, g_anti = 0;
+    GenConst* d_gc = nullptr;
     // grids: the split layout (bin-major, uniform grids) and/or the bins layout
     // ([group][node][lane] per grid); small uniform grids keep both so that the
     // autotuner can choose the mapping
@@ -451,6 +457,7 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
 
 gna_status check_eval_args(gna_plan* plan, const gna_osc* params, const double* data, const gna_outputs* out, int dpp) {
     if (!plan) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "an any-channel plan is evaluated by gna_chain_eval_general");
     if (!params || !data || !out || !out->chi2) return fail(plan, GNA_EINVAL, "params, data, out and out->chi2 are required");
     if (dpp && plan->max_datasets < plan->npts)
         return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
@@ -796,6 +803,18 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     plan->max_datasets = std::max(d->max_datasets, d->npts);
     plan->ph = (d->prec == GNA_MIXED_FFPHASE) ? 0 : (d->prec == GNA_MIXED_F64PHASE) ? 1 : 2;
     plan->nl_inst = inst_nl(d->nL, plan->ph);
+    plan->general = (d->flags & GNA_PLAN_GENERAL) != 0;
+    if (plan->general) {
+        if (plan->ph == 2) return fail(plan, GNA_EINVAL, "the any-channel chain runs in the mixed precisions");
+        if (d->nL > 8) return fail(plan, GNA_ESHAPE, "the any-channel chain takes up to 8 baselines");
+        if (d->alpha < 0 || d->alpha > 2 || d->beta < 0 || d->beta > 2 || (d->anti != 0 && d->anti != 1))
+            return fail(plan, GNA_EINVAL, "alpha and beta must be 0..2 and anti 0 or 1");
+        if (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_WITH_PLAIN))
+            return fail(plan, GNA_EINVAL, "the any-channel chain has the bin and slice mappings only, no plain chain");
+        plan->g_alpha = d->alpha;
+        plan->g_beta = d->beta;
+        plan->g_anti = d->anti;
+    }
     plan->edges.assign(d->edges, d->edges + d->nbins + 1);
     plan->L.assign(d->L, d->L + d->nL);
     // baseline weights
@@ -842,14 +861,16 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     // groups alone do not (estimate: 16 resident warps per SM)
     const int64_t warps_est = 16LL * plan->sm_count;
     const bool slices_ok = plan->uniform && plan->ph < 2;
-    if (d->flags & GNA_PLAN_FORCE_SPLIT) plan->mapping = MAP_SPLIT;
+    if (plan->general) plan->mapping = (plan->uniform && !(d->flags & GNA_PLAN_FORCE_BINS)) ? MAP_SLICES : MAP_BINS;
+    else if (d->flags & GNA_PLAN_FORCE_SPLIT) plan->mapping = MAP_SPLIT;
     else if (d->flags & GNA_PLAN_FORCE_BINS) plan->mapping = MAP_BINS;
     else if (d->flags & GNA_PLAN_FORCE_SLICES) plan->mapping = MAP_SLICES;
     else if (slices_ok && (int64_t)d->npts * ngroups < 4 * warps_est) plan->mapping = MAP_SLICES;
     else if (plan->uniform && (plan->n_uniform >= 1024 || (int64_t)d->npts * ngroups < 16LL * plan->sm_count))
         plan->mapping = MAP_SPLIT;
     else plan->mapping = MAP_BINS;
-    const bool forced = (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_BINS | GNA_PLAN_FORCE_SLICES)) != 0;
+    const bool forced = plan->general ||
+                        (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_FORCE_BINS | GNA_PLAN_FORCE_SLICES)) != 0;
     const bool small = plan->uniform && (int64_t)d->nbins * plan->n_uniform <= (1LL << 20) &&
                        (int64_t)d->npts * d->nbins <= (1LL << 16);
     // a default slice mapping keeps the split layout too (grids up to 2^26
@@ -966,7 +987,8 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     TRY(dalloc(plan, &plan->d_counters, plan->ncounters));
     // scratch
     TRY(dalloc(plan, &plan->d_pc, d->npts));
-    const int nv_max = fused_nv(plan->nl_inst, true, true);
+    if (plan->general) TRY(dalloc(plan, &plan->d_gc, d->npts));
+    const int nv_max = std::max(fused_nv(plan->nl_inst, true, true), plan->general ? 12 : 0);
     if (plan->has_split) {
         // ranges are at least 128 nodes long, so a bin meets at most ceil(n / 128) + 1 of
         // them; the slot count is capped so that the partials stay within 256 M values
@@ -988,7 +1010,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     }
     TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
     TRY(dalloc(plan, &plan->d_gvals, (size_t)d->npts * ngroups * 15));
-    if ((int64_t)d->npts * d->nbins * nv_max <= (32LL << 20))  // up to 256 MB
+    if (!plan->general && (int64_t)d->npts * d->nbins * nv_max <= (32LL << 20))  // up to 256 MB
         TRY(dalloc(plan, &plan->d_binsums, (size_t)d->npts * d->nbins * nv_max));
     TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
     TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
@@ -1114,9 +1136,51 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
     return GNA_OK;
 }
 
+gna_status gna_chain_eval_general(gna_plan* plan, const gna_osc_full* params, const double* eta, double sigma_eta,
+                                  const double* data, int data_per_point, const gna_outputs* out, void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (!plan->general) return fail(plan, GNA_ESTATE, "the plan was created for the nue_bar survival chain");
+    if (!params || !data || !out || !out->chi2) return fail(plan, GNA_EINVAL, "params, data, out and out->chi2 are required");
+    if (out->spectra) return fail(plan, GNA_EINVAL, "the any-channel chain has no per-baseline spectra");
+    if (data_per_point && plan->max_datasets < plan->npts)
+        return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    const bool grad = out->grad || out->grad_eta;
+    const int NV = grad ? 12 : 6;
+    SliceShape ssh{1, 0, plan->ntasks};
+    if (plan->mapping == MAP_SLICES) {
+        ssh = slice_shape(plan);
+        if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
+    }
+    const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups);
+    CU(launch_prepare_general(params, plan->npts, plan->bc, plan->g_alpha, plan->g_beta, plan->g_anti, plan->d_pc,
+                              plan->d_gc, plan->d_counters, ncnt, plan->d_status, s));
+    EvalReq q{nullptr, eta, sigma_eta, data, data_per_point, out->chi2, out->grad, out->grad_eta, out->mu, nullptr,
+              nullptr};
+    EpiArgs ea = make_epi(plan, q, grad, false, NV);
+    ea.NBV = grad ? 7 : 1;  // chi2 and the six-parameter gradient terms
+    ea.binsums = nullptr;
+    const bool sliced = ssh.S > 1;
+    int64_t g = (int64_t)plan->sm_count * general_resident_ctas(plan->ph, plan->nl_inst, grad, plan->block);
+    g = std::max<int64_t>(1, std::min<int64_t>(g, ((int64_t)ssh.ntasks * 32 + plan->block - 1) / plan->block));
+    GenArgs ga{BinArgs{plan->grid_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, ssh.ntasks,
+                       plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, ssh.S, ssh.L,
+                       sliced ? plan->d_slices : nullptr},
+               plan->d_gc};
+    CU(dispatch_general(plan->ph, plan->nl_inst, grad, ga, (int)g, plan->block, s));
+    plan->last_launches = 2;
+    if (sliced) {
+        CU(launch_slices_reduce_general(plan->d_slices, ssh.S, NV, ea, plan->d_gc, plan->npts, s));
+        plan->last_launches = 3;
+    }
+    return GNA_OK;
+}
+
 gna_status gna_chain_eval_cached(gna_plan* plan, const double* eta, double sigma_eta, const double* data,
                                  int data_per_point, const gna_outputs* out, void* stream) {
     if (!plan || !out || !out->chi2 || !data) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "not available for an any-channel plan");
     if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
     if (!plan->d_binsums) return fail(plan, GNA_ESHAPE, "the plan keeps no node sums (points x bins too large)");
     if (!plan->cache_valid) return fail(plan, GNA_ESTATE, "no evaluation has kept node sums yet");
@@ -1143,6 +1207,7 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
                                      const double* data, int data_per_point, int grad, int spectra, void* stream,
                                      int64_t* ticket) {
     if (!plan) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "not available for an any-channel plan");
     if (!params || !data || !ticket) return fail(plan, GNA_EINVAL, "params, data and ticket are required");
     if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
     const size_t n_spec = (size_t)plan->npts * plan->nL * plan->nbins;
@@ -1293,6 +1358,7 @@ gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const dou
 gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, int iters, double lambda0, double* chi2_out,
                          int use_graph, void* stream) {
     if (!plan) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "not available for an any-channel plan");
     if (!params || !data || !chi2_out) return fail(plan, GNA_EINVAL, "params, data and chi2_out are required");
     if (iters < 1) return fail(plan, GNA_EINVAL, "iters must be >= 1");
     if (plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "fits need one data row per point");
@@ -1371,6 +1437,8 @@ gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     }
     if (block < 32 || block > 256 || (block & 31) || npt < 1 || npt > 1024 || gm < 0 || gm > 64 || sl < 0)
         return fail(plan, GNA_EINVAL, "bad tuning '%s'", text);
+    if (plan->general && mapping != plan->mapping)
+        return fail(plan, GNA_EINVAL, "an any-channel plan keeps the mapping it was created with");
     if ((mapping == MAP_SPLIT && !plan->has_split) || (mapping == MAP_BINS && !plan->has_bins) ||
         (mapping == MAP_SLICES && (!plan->has_bins || !plan->uniform || plan->ph == 2)))
         return fail(plan, GNA_EINVAL, "the plan has no grid for the %s mapping",
@@ -1388,6 +1456,7 @@ gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
 gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point,
                              const gna_outputs* out, int reps, void* stream) {
     if (!plan || !params || !data) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "not available for an any-channel plan");
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
     // candidates are timed the way the plan will run them (graph replay when

@@ -642,3 +642,97 @@ def test_bad_arguments_raise(api):
         plan.tuning = "block=1000"
     with pytest.raises(N.GnaError):
         api.Plan([1.0, 2.0], list(range(1, 18)), nodes_per_bin=4)
+
+
+# ------------------------------------------------------ any-channel chain --
+GEN_TH = np.array([0.307, 0.0218, 0.545, 1.2 * np.pi, 7.53e-5, 2.44e-3])
+
+
+def general_case(channel, edges, counts, L, npts, e_scale, kind, seed, nuisances=False):
+    """Points near GEN_TH, Poisson data from the oracle's prediction at GEN_TH
+    (largest node count), normalised to 10^4 events."""
+    a, b, anti = channel
+    rng = np.random.default_rng(seed)
+    theta = np.tile(GEN_TH, (npts, 1)) * rng.uniform(0.97, 1.03, size=(npts, 6))
+    counts = np.broadcast_to(np.asarray(counts), (npts,)).astype(np.int32)
+    n_t = int(counts.max())
+    mu_rb, _ = oracle.binned_general(edges, n_t, L, GEN_TH, a, b, anti, e_scale)
+    M = oracle.baseline_weights(np.atleast_1d(L)) @ mu_rb
+    N = 1e4 / M.sum()
+    data = wl.poisson_data(N * M, seed + 100)
+    eta = rng.normal(0.0, 0.02, edges.size - 1) if nuisances else None
+    refs = [oracle.chain_general(edges, int(counts[p]), L, theta[p], N, data, a, b, anti, kind, eta,
+                                 0.02 if nuisances else 0.0, e_scale) for p in range(npts)]
+    return theta, counts, N, data, eta, refs
+
+
+def check_general(api, channel, prec, edges, counts, L, npts, e_scale, kind, seed, nuisances=False, uniform=True):
+    theta, counts, N, data, eta, refs = general_case(channel, edges, counts, L, npts, e_scale, kind, seed, nuisances)
+    kw = dict(nodes_per_bin=int(counts[0])) if uniform else dict(node_counts=counts)
+    plan = api.Plan(edges, L, npts=npts, norm=N, e_scale=e_scale, prec=prec, kind=KIND_NAMES[kind],
+                    channel=channel, **kw)
+    out = plan.eval_general(plan.params_tensor(theta), dev(data), None if eta is None else dev(eta),
+                            0.02 if nuisances else 0.0, grad=True, grad_eta=nuisances, mu=True)
+    torch.cuda.synchronize()
+    plan.status()
+    for p in range(npts):
+        ref = refs[p]
+        assert abs(out["chi2"][p].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, data, kind), p
+        assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < 1e-6, p
+        assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:6]) < 1e-4, p
+        if nuisances:
+            assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][6:]) < 1e-4, p
+    plan.close()
+
+
+KIND_NAMES = {0: "pearson", 1: "poisson"}
+CHANNELS = [("mu", "e", False), ("mu", "mu", False), ("mu", "e", True), ("e", "e", True), ("e", "tau", False)]
+
+
+@pytest.mark.parametrize("channel", CHANNELS)
+@pytest.mark.parametrize("prec", ["ff", "f64phase"])
+def test_general_chain_long_baseline(api, channel, prec):
+    # 810 km, 0.5-5 GeV (energies in MeV, spectrum in GeV), 3 points on one
+    # grid of 40 bins x 24 nodes: the slice mapping
+    check_general(api, channel, prec, np.linspace(500.0, 5000.0, 41), 24, np.array([810.0]), 3, 1e-3, 1, 7)
+
+
+@pytest.mark.parametrize("channel", [("mu", "e", False), ("e", "e", True)])
+def test_general_chain_uneven_grids_baselines_nuisances(api, channel):
+    # per-point node counts (two points share one), three baselines (four-baseline
+    # kernel with a zero-weight slot), Pearson chi^2 with nuisances: the bin mapping
+    check_general(api, channel, "ff", np.linspace(500.0, 5000.0, 71), [12, 30, 12, 7], np.array([810.0, 295.0, 1300.0]),
+                  4, 1e-3, 0, 9, nuisances=True, uniform=False)
+
+
+def test_general_chain_reactor_many_nodes(api):
+    # nue_bar survival through the any-channel chain on a reactor-like grid of
+    # 20 bins x 2048 nodes and eight baselines (slices of the nodes)
+    check_general(api, ("e", "e", True), "ff", np.linspace(1.8, 9.0, 21), 2048,
+                  np.array([52.5, 52.8, 53.0, 52.2, 1.6, 1.9, 5.0, 40.0]), 1, 1.0, 1, 11)
+
+
+def test_general_plan_calls_and_status(api):
+    edges = np.linspace(500.0, 5000.0, 11)
+    gp = api.Plan(edges, [810.0], nodes_per_bin=8, e_scale=1e-3, channel=("mu", "e", False))
+    d = torch.full((10,), 50.0, dtype=torch.float64, device="cuda")
+    from paper_1804_07682_gb300 import _native as N
+    with pytest.raises(N.GnaError):  # the survival-chain call on an any-channel plan
+        gp.eval(torch.zeros(1, 4, dtype=torch.float64, device="cuda"), d)
+    ep = api.Plan(edges, [810.0], nodes_per_bin=8, e_scale=1e-3)
+    with pytest.raises(ValueError):
+        ep.eval_general(torch.zeros(1, 6, dtype=torch.float64, device="cuda"), d)
+    ep.close()
+    # a mixing parameter on the boundary is reported by status()
+    bad = GEN_TH.copy()
+    bad[2] = 0.0
+    gp.eval_general(gp.params_tensor(bad), d)
+    torch.cuda.synchronize()
+    with pytest.raises(N.GnaError):
+        gp.status()
+    gp.eval_general(gp.params_tensor(GEN_TH), d)
+    torch.cuda.synchronize()
+    gp.status()
+    gp.close()
+    with pytest.raises(N.GnaError):  # FP64 is not offered for the any-channel chain
+        api.Plan(edges, [810.0], nodes_per_bin=8, prec="fp64", channel=("mu", "e", False))

@@ -36,6 +36,17 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
+def fp32_ops_general(nL: int, grad: bool) -> int:
+    """Algorithmic FP32 operations per energy node of the any-channel node
+    kernel: per (node, baseline) the phases and their sin/cos 38, angle
+    addition 4, sin^2 and sin cos of three phases 6, their weighted sums 6
+    (12 with hi + lo weights for several baselines), with the gradient
+    cos^2 - sin^2 3 and two more weighted sums per phase 6; per node the Kahan
+    product-sums of 6 (12) values, 4 each."""
+    per_r = 54 + (6 if nL > 1 else 0) + (9 if grad else 0)
+    return nL * per_r + (48 if grad else 24)
+
+
 def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     """Algorithmic FP32 operations (FMA = 1) of the fused kernel per energy node.
 
@@ -275,6 +286,46 @@ def side_workloads(api, torch, device, args):
                                  "fp32_frac_of_issue_peak": ops / (ms * 1e-3) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
                                  "tuning": plan.tuning, "graph": True}
     plan.close()
+    # the same scan for nu_mu -> nu_e appearance through the any-channel chain:
+    # (s2_13, dm2_32) on the same uneven grids, s2_23 = 0.545 and delta = 1.2 pi,
+    # chi^2 and its gradient in all six parameters
+    def six(t):
+        t = np.atleast_2d(t)
+        k = t.shape[0]
+        return np.column_stack([t[:, 0], t[:, 1], np.full(k, 0.545), np.full(k, 1.2 * np.pi), t[:, 2], t[:, 3]])
+
+    gkw = dict(npts=w.npts, node_counts=w.node_counts, e_scale=w.e_scale, prec=args.prec, kind=w.kind,
+               channel=("mu", "e", False))
+    plan = api.Plan(w.edges, w.L, norm=1.0, **gkw)
+    m = plan.eval_general(plan.params_tensor(six(np.repeat(np.array(wl.TRUTH)[None, :], w.npts, axis=0))), dummy,
+                          grad=False, mu=True)["mu"][int(np.argmax(w.node_counts))]
+    Ng = wl.TOTAL_EVENTS / float(m.sum())
+    plan.close()
+    plan = api.Plan(w.edges, w.L, norm=Ng, **gkw)
+    th6 = six(w.theta)
+    pg = plan.params_tensor(th6)
+    datag = torch.as_tensor(wl.poisson_data((m * Ng).cpu().numpy(), w.data_seed), device=device)
+    plan.autotune(pg, datag, reps=3)
+    og = {"chi2": torch.empty(w.npts, dtype=torch.float64, device=device),
+          "grad": torch.empty(w.npts, 6, dtype=torch.float64, device=device)}
+    for _ in range(3):
+        plan.eval_general(pg, datag, grad=True, out=og)
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    for _ in range(reps):
+        plan.eval_general(pg, datag, grad=True, out=og)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / reps
+    ops = sum(fp32_ops_general(1, True) * w.nbins * int(n) for n in w.node_counts)
+    check["scan_numu_nue"] = (w, Ng, datag.cpu().numpy(), og["chi2"].cpu().numpy(), og["grad"].cpu().numpy(), th6)
+    out["scan_64x64_500bins_numu_nue"] = {
+        "scans_per_s": 1e3 / ms, "ms_per_scan": ms, "chi2_grad_evals_per_s": w.npts * 1e3 / ms,
+        "gpoints_per_s": pts / ms / 1e6,
+        "fp32_frac_of_issue_peak": ops / (ms * 1e-3) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
+        "outputs": "chi2, d chi2 / d(s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32)", "tuning": plan.tuning}
+    plan.close()
     # fits
     w = wl.fits_16384x1000()
     plan = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, npts=1, norm=1.0, prec=args.prec, kind=w.kind)
@@ -482,6 +533,14 @@ def cpu_side_errors(side, check):
         e["chi2"] = max(e["chi2"], rmax(c2[p], r["chi2"]))
         e["grad_normwise"] = max(e["grad_normwise"], nrel(g[p], r["grad"][:4]))
     side["scan_64x64_500bins"]["error_vs_oracle"] = e
+    w, N, d, c2, g, th6 = check["scan_numu_nue"]
+    e = {"points": [0, 2049, 4095], "chi2": 0.0, "grad_normwise": 0.0}
+    for p in e["points"]:
+        r = oracle.chain_general(w.edges, int(w.node_counts[p]), w.L, th6[p], N, d, "mu", "e", False, w.kind,
+                                 e_scale=w.e_scale)
+        e["chi2"] = max(e["chi2"], rmax(c2[p], r["chi2"]))
+        e["grad_normwise"] = max(e["grad_normwise"], nrel(g[p], r["grad"][:6]))
+    side["scan_64x64_500bins_numu_nue"]["error_vs_oracle"] = e
     w, N, d, c2, g, ge = check["nuisance"]
     r = oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], N, d, w.kind, eta=w.eta, sigma=w.sigma_eta)
     side["nuisance_1000x4096"]["error_vs_oracle"] = {

@@ -380,6 +380,11 @@ gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, in
  */
 gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point,
                              const gna_outputs* out, int reps, void* stream);
+/* gna_plan_autotune_general: the same for an any-channel plan (params:
+ * device [npts] gna_osc_full; out required, as for gna_chain_eval_general):
+ * threads per block and, with the slice mapping, the slice length. */
+gna_status gna_plan_autotune_general(gna_plan* plan, const gna_osc_full* params, const double* data,
+                                     int data_per_point, const gna_outputs* out, int reps, void* stream);
 gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen);
 gna_status gna_plan_set_tuning(gna_plan* plan, const char* text);
 

@@ -92,6 +92,7 @@ SIGNATURES = {
                                      ctypes.POINTER(GnaOutputs), c_void_p]),
     "gna_fit_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p, c_int, c_void_p]),
     "gna_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p]),
+    "gna_plan_autotune_general": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p]),
     "gna_plan_get_tuning": (c_int, [c_void_p, c_char_p, c_int]),
     "gna_plan_set_tuning": (c_int, [c_void_p, c_char_p]),
     "gna_plan_set_graph": (c_int, [c_void_p, c_int]),

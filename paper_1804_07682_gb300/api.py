@@ -430,9 +430,15 @@ class Plan:
         dpp = 1 if data.dim() == 2 else 0
         out = {"chi2": self._out("chi2", (self.npts,))}
         if grad:
-            out["grad"] = self._out("grad", (self.npts, 4))
+            out["grad"] = self._out("grad", (self.npts, 4 if self.channel is None else 6))
         if mu:
             out["mu"] = self._out("mu", (self.npts, self.nbins))
+        if self.channel is not None:
+            o = N.GnaOutputs(_ptr(out["chi2"]), _ptr(out.get("grad")), None, _ptr(out.get("mu")), None)
+            code = self._lib.gna_plan_autotune_general(self._h, _ptr(params), _ptr(data), dpp, ctypes.byref(o),
+                                                       int(reps), ctypes.c_void_p(_stream(stream)))
+            self._check(code, "gna_plan_autotune_general")
+            return self.tuning
         if spectra:
             out["spectra"] = self._out("spectra", (self.npts, self.nL, self.nbins))
         o = N.GnaOutputs(_ptr(out["chi2"]), _ptr(out.get("grad")), None, _ptr(out.get("mu")), _ptr(out.get("spectra")))

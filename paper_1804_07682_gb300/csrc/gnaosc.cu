@@ -1453,6 +1453,39 @@ gna_status gna_plan_set_tuning(gna_plan* plan, const char* text) {
     return GNA_OK;
 }
 
+// Times each tuning candidate (a warm-up call, then reps calls between two
+// events on the stream) and keeps the fastest; the plan's tuning is restored
+// when no candidate runs.
+extern "C++" template <typename Eval>
+gna_status time_candidates(gna_plan* plan, const std::vector<std::string>& cand, int reps, cudaStream_t s, Eval eval) {
+    char best_t[128];
+    gna_plan_get_tuning(plan, best_t, sizeof(best_t));
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (const std::string& c : cand) {
+        if (gna_plan_set_tuning(plan, c.c_str()) != GNA_OK) continue;
+        if (eval() != GNA_OK) continue;  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; r++) eval();
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            snprintf(best_t, sizeof(best_t), "%s", c.c_str());
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    gna_status st = gna_plan_set_tuning(plan, best_t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    return st;
+}
+
 gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double* data, int data_per_point,
                              const gna_outputs* out, int reps, void* stream) {
     if (!plan || !params || !data) return GNA_EINVAL;
@@ -1490,34 +1523,36 @@ gna_status gna_plan_autotune(gna_plan* plan, const gna_osc* params, const double
                 cand.push_back(t);
             }
     }
-    char best_t[128];
-    gna_plan_get_tuning(plan, best_t, sizeof(best_t));
-    float best = 1e30f;
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
     const gna_outputs o = out ? *out : gna_outputs{plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr};
-    for (const std::string& c : cand) {
-        if (gna_plan_set_tuning(plan, c.c_str()) != GNA_OK) continue;
-        gna_status st = gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);  // warm-up
-        if (st != GNA_OK) continue;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; r++) gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            snprintf(best_t, sizeof(best_t), "%s", c.c_str());
+    return time_candidates(plan, cand, reps, s, [&]() {
+        return gna_chain_eval(plan, params, nullptr, 0.0, data, data_per_point, &o, stream);
+    });
+}
+
+gna_status gna_plan_autotune_general(gna_plan* plan, const gna_osc_full* params, const double* data,
+                                     int data_per_point, const gna_outputs* out, int reps, void* stream) {
+    if (!plan || !params || !data || !out || !out->chi2) return GNA_EINVAL;
+    if (!plan->general) return fail(plan, GNA_ESTATE, "the plan was created for the nue_bar survival chain");
+    if (reps < 1) reps = 3;
+    std::vector<std::string> cand;
+    char t[96];
+    for (int b : {64, 128, 256}) {
+        if (plan->mapping == MAP_BINS) {
+            snprintf(t, sizeof(t), "mapping=bins block=%d", b);
+            cand.push_back(t);
+        } else {
+            const int64_t pg = (int64_t)plan->npts * plan->ngroups;
+            for (int tpw : {1, 2, 4}) {
+                const int64_t S = std::max<int64_t>(1, ((int64_t)tpw * 16 * plan->sm_count + pg - 1) / pg);
+                const int64_t L = std::min<int64_t>(plan->n_uniform, (plan->n_uniform + S - 1) / S);
+                snprintf(t, sizeof(t), "mapping=slices block=%d slice=%lld", b, (long long)L);
+                cand.push_back(t);
+            }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    gna_status st = gna_plan_set_tuning(plan, best_t);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(plan, GNA_ECUDA, "autotune: %s", cudaGetErrorString(e));
-    return st;
+    return time_candidates(plan, cand, reps, (cudaStream_t)stream, [&]() {
+        return gna_chain_eval_general(plan, params, nullptr, 0.0, data, data_per_point, out, stream);
+    });
 }
 
 gna_status gna_plan_set_graph(gna_plan* plan, int on) {

@@ -675,10 +675,18 @@ def check_general(api, channel, prec, edges, counts, L, npts, e_scale, kind, see
                             0.02 if nuisances else 0.0, grad=True, grad_eta=nuisances, mu=True)
     torch.cuda.synchronize()
     plan.status()
+    # the FP32 rounding of sin^2 bounds the error of a node's P absolutely
+    # (~1e-7), so mu is held to 1e-6 relative plus 1e-7 of the bin's count at
+    # P = 1 (a disappearance dip turns the absolute bound into a larger
+    # relative one)
+    L1 = np.atleast_1d(L)
     for p in range(npts):
         ref = refs[p]
+        flat = oracle.baseline_weights(L1) @ oracle.binned(edges, int(counts[p]), L1, (0.3, 0.02, 0.0, 0.0), e_scale)
+        scale = N * (1.0 + (0.0 if eta is None else eta)) * flat
         assert abs(out["chi2"][p].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, data, kind), p
-        assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < 1e-6, p
+        err = np.abs(out["mu"][p].cpu().numpy() - ref["mu"])
+        assert np.all(err <= 1e-6 * np.abs(ref["mu"]) + 1e-7 * scale), (p, float((err / ref["mu"]).max()))
         assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:6]) < 1e-4, p
         if nuisances:
             assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][6:]) < 1e-4, p
@@ -733,6 +741,12 @@ def test_general_plan_calls_and_status(api):
     gp.eval_general(gp.params_tensor(GEN_TH), d)
     torch.cuda.synchronize()
     gp.status()
+    # the autotuner times block sizes and slice lengths of the plan's mapping
+    tuning = gp.autotune(gp.params_tensor(GEN_TH), d, reps=1)
+    assert tuning.startswith("mapping=slices")
+    r = gp.eval_general(gp.params_tensor(GEN_TH), d, mu=True)
+    ref = oracle.chain_general(edges, 8, [810.0], GEN_TH, 1.0, d.cpu().numpy(), "mu", "e", kind=0, e_scale=1e-3)
+    assert rel(r["chi2"][0].item(), ref["chi2"]) < 1e-6
     gp.close()
     with pytest.raises(N.GnaError):  # FP64 is not offered for the any-channel chain
         api.Plan(edges, [810.0], nodes_per_bin=8, prec="fp64", channel=("mu", "e", False))

@@ -95,9 +95,13 @@ __device__ void general_coefficients(const gna_osc_full& o, int alpha, int beta,
         const double sb = anti ? -4.0 : 4.0;
         gc.a[k] = -4.0 * X.re.v;
         gc.b[k] = sb * X.im.v;
+        gc.af[k] = (float)gc.a[k];
+        gc.bf[k] = (float)gc.b[k];
         for (int q = 0; q < 4; q++) {
             gc.da[q][k] = -4.0 * X.re.d[q];
             gc.db[q][k] = sb * X.im.d[q];
+            gc.daf[q][k] = (float)gc.da[q][k];
+            gc.dbf[q][k] = (float)gc.db[q][k];
         }
     }
 }

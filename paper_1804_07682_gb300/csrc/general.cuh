@@ -34,6 +34,9 @@ struct GenConst {
     double a[3], b[3]; // pairs (21, 31, 32)
     double da[4][3];   // d a / d(s2_12, s2_13, s2_23, delta)
     double db[4][3];
+    // FP32 copies for the gradient terms (FP64 instructions run at 1/64 of
+    // the FP32 rate on this part; the gradient is held to 1e-4)
+    float af[3], bf[3], daf[4][3], dbf[4][3];
 };
 
 struct GenArgs {
@@ -114,15 +117,16 @@ struct NodeMathGen {
     }
 };
 
-// Bin i of point p from its summed values v = [U(3), V(3)] (+ [Y(3), Z(3)])
-// and the point's coefficients: M and its six derivatives, then the chi^2
-// term and its gradient contributions into regs[0..6] (double-float pairs):
-// [0] the chi^2 term, [1 + q] g_i N (1 + eta_i) dM/dp_q.
-__device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int p, int i, const double* v,
-                                        const BinIn& in, float2* regs) {
+// Bin i of point p from its summed values [U(3), V(3)] (+ [Y(3), Z(3)]):
+// vd the first six in double, vf all of them in FP32, and the point's
+// coefficients: M in double (its terms may cancel), its six derivatives in
+// FP32, then the chi^2 term and its gradient contributions into
+// regs[0..6] (float pairs): [0] the chi^2 term, [1 + q] g_i N (1 + eta_i) dM/dp_q.
+__device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int p, int i, const double* vd,
+                                        const float* vf, const BinIn& in, float2* regs) {
     const int64_t idx = (int64_t)p * a.nbins + i;
     double M = c.dab * in.sumw;
-    for (int j = 0; j < 3; j++) M += c.a[j] * v[j] + c.b[j] * v[3 + j];
+    for (int j = 0; j < 3; j++) M += c.a[j] * vd[j] + c.b[j] * vd[3 + j];
     const double e = in.e;
     const double f = a.norm * (1.0 + e);
     const double mu = f * M;
@@ -139,16 +143,17 @@ __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int
     if (pen) term += e * e / (a.sigma * a.sigma);
     regs[0] = to_ff(term);
     if (a.has_grad) {
-        double dM[6];
+        float dM[6];
         for (int q = 0; q < 4; q++) {
-            dM[q] = 0.0;
-            for (int j = 0; j < 3; j++) dM[q] += c.da[q][j] * v[j] + c.db[q][j] * v[3 + j];
+            dM[q] = 0.f;
+            for (int j = 0; j < 3; j++) dM[q] = fmaf(c.daf[q][j], vf[j], fmaf(c.dbf[q][j], vf[3 + j], dM[q]));
         }
         // pairs 0 = 21, 1 = 31, 2 = 32; x31 moves with both splittings
-        const double t31 = c.a[1] * v[7] + 0.5 * c.b[1] * v[10];
-        dM[4] = c.a[0] * v[6] + 0.5 * c.b[0] * v[9] + t31;
-        dM[5] = c.a[2] * v[8] + 0.5 * c.b[2] * v[11] + t31;
-        for (int q = 0; q < 6; q++) regs[1 + q] = to_ff(gd * f * dM[q]);
+        const float t31 = fmaf(c.af[1], vf[7], 0.5f * c.bf[1] * vf[10]);
+        dM[4] = fmaf(c.af[0], vf[6], fmaf(0.5f * c.bf[0], vf[9], t31));
+        dM[5] = fmaf(c.af[2], vf[8], fmaf(0.5f * c.bf[2], vf[11], t31));
+        const float gf = (float)(gd * f);
+        for (int q = 0; q < 6; q++) regs[1 + q] = make_float2(gf * dM[q], 0.f);
     }
     if (a.mu_out) a.mu_out[idx] = mu;
     if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
@@ -258,10 +263,13 @@ __global__ void __launch_bounds__(256) k_fused_bins_gen(GenArgs ga) {
         const int i = b * 32 + lane;
         float2 regs[15];
         if (i < a.nbins) {
-            double v[NV];
+            double vd[6];
+            float vf[12];
 #pragma unroll
-            for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
-            gen_bin_epilogue(a.ea, ga.gc[p], p, i, v, bin_inputs(a.ea, p, i), regs);
+            for (int j = 0; j < 6; j++) vd[j] = (double)acc[j].s - (double)acc[j].c;
+#pragma unroll
+            for (int j = 0; j < NV; j++) vf[j] = acc[j].s - acc[j].c;
+            gen_bin_epilogue(a.ea, ga.gc[p], p, i, vd, vf, bin_inputs(a.ea, p, i), regs);
         }
         gen_group_done(a.ea, p, b, lane, regs);
     }
@@ -304,17 +312,23 @@ __global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __re
     for (int v = 0; v < NVM; v++)
         if (v < NV) red[(w * NV + v) * 32 + lane] = acc[v];
     __syncthreads();
+    float2* fin2 = reinterpret_cast<float2*>(fin);
     for (int v = w; v < NV; v += W) {
         float2 sum = red[v * 32 + lane];
         for (int k = 1; k < W; k++) sum = ff_add(sum, red[(k * NV + v) * 32 + lane]);
-        fin[v * 32 + lane] = (double)sum.x + (double)sum.y;
+        fin2[v * 32 + lane] = sum;
     }
     __syncthreads();
     if (w == 0) {
-        double vals[NVM];
-        for (int v = 0; v < NV; v++) vals[v] = fin[v * 32 + lane];
+        double vd[6];
+        float vf[NVM];
+        for (int v = 0; v < NV; v++) {
+            const float2 t = fin2[v * 32 + lane];
+            vf[v] = t.x + t.y;
+            if (v < 6) vd[v] = (double)t.x + (double)t.y;
+        }
         float2 regs[15];
-        if (i < ea.nbins) gen_bin_epilogue(ea, gc[p], p, i, vals, in, regs);
+        if (i < ea.nbins) gen_bin_epilogue(ea, gc[p], p, i, vd, vf, in, regs);
         gen_group_done(ea, p, g, lane, regs);
     }
 }

@@ -804,13 +804,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     plan->ph = (d->prec == GNA_MIXED_FFPHASE) ? 0 : (d->prec == GNA_MIXED_F64PHASE) ? 1 : 2;
     plan->nl_inst = inst_nl(d->nL, plan->ph);
     plan->general = (d->flags & GNA_PLAN_GENERAL) != 0;
-    if (plan->general) {
-        if (plan->ph == 2) return fail(plan, GNA_EINVAL, "the any-channel chain runs in the mixed precisions");
-        if (d->nL > 8) return fail(plan, GNA_ESHAPE, "the any-channel chain takes up to 8 baselines");
-        if (d->alpha < 0 || d->alpha > 2 || d->beta < 0 || d->beta > 2 || (d->anti != 0 && d->anti != 1))
-            return fail(plan, GNA_EINVAL, "alpha and beta must be 0..2 and anti 0 or 1");
-        if (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_WITH_PLAIN))
-            return fail(plan, GNA_EINVAL, "the any-channel chain has the bin and slice mappings only, no plain chain");
+    if (plan->general) {  // the descriptor was checked by gna_plan_create
         plan->g_alpha = d->alpha;
         plan->g_beta = d->beta;
         plan->g_anti = d->anti;
@@ -1065,6 +1059,12 @@ gna_status gna_plan_create(gna_plan** out, const gna_plan_desc* d, void* stream)
         if (!d->node_counts) break;
     }
     if (!(d->norm > 0.0)) return GNA_EINVAL;
+    if (d->flags & GNA_PLAN_GENERAL) {
+        if (d->prec == GNA_FP64 || (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_WITH_PLAIN))) return GNA_EINVAL;
+        if (d->alpha < 0 || d->alpha > 2 || d->beta < 0 || d->beta > 2 || (d->anti != 0 && d->anti != 1))
+            return GNA_EINVAL;
+        if (d->nL > 8) return GNA_ESHAPE;
+    }
     gna_plan* plan = new gna_plan();
     gna_status st = plan_build(plan, d, (cudaStream_t)stream);
     if (st != GNA_OK) {

@@ -22,7 +22,7 @@ def desc(N, **kw):
     edges = np.linspace(1.8, 8.0, 11)
     L = np.array([52.5, 53.1])
     d = dict(nbins=10, edges=edges, nodes_per_bin=8, npts=1, node_counts=None, nL=2, L=L, Lweight=None, norm=1.0,
-             e_scale=1.0, prec=2, kind=1, max_datasets=0, flags=0)
+             e_scale=1.0, prec=2, kind=1, max_datasets=0, flags=0, alpha=0, beta=0, anti=0)
     d.update(kw)
     keep = [d["edges"], d["L"], d["Lweight"], d["node_counts"]]
     D = N.GnaPlanDesc()
@@ -38,6 +38,7 @@ def desc(N, **kw):
         D.Lweight = d["Lweight"].ctypes.data_as(DBL)
     D.norm, D.e_scale, D.prec, D.kind = d["norm"], d["e_scale"], d["prec"], d["kind"]
     D.max_datasets, D.flags = d["max_datasets"], d["flags"]
+    D.alpha, D.beta, D.anti = d["alpha"], d["beta"], d["anti"]
     return D, keep
 
 
@@ -59,6 +60,15 @@ def desc(N, **kw):
     (dict(norm=float("nan")), EINVAL),
     (dict(prec=3), EINVAL),
     (dict(kind=2), EINVAL),
+    # any-channel plans: mixed precisions, flavours 0..2, anti 0 or 1, up to 8
+    # baselines, no split mapping or plain chain
+    (dict(flags=16, prec=0), EINVAL),
+    (dict(flags=16, alpha=3), EINVAL),
+    (dict(flags=16, beta=-1), EINVAL),
+    (dict(flags=16, anti=2), EINVAL),
+    (dict(flags=16 | 2), EINVAL),
+    (dict(flags=16 | 1), EINVAL),
+    (dict(flags=16, nL=9, L=np.linspace(1.0, 9.0, 9)), ESHAPE),
 ])
 def test_plan_descriptor_is_checked_on_the_host(N, kw, code):
     D, keep = desc(N, **kw)

@@ -284,7 +284,8 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
  * the three phases, and their derivatives in the phases); the epilogue
  * contracts them with the point's coefficients -4 Re X_ij, 4 Im X_ij and
  * their derivatives, X_ij = V*_ai V_bi V_aj V*_bj.  Asynchronous on
- * `stream`; GNA_ESTATE on a survival-chain plan.
+ * `stream` (launched directly: graph mode applies to gna_chain_eval);
+ * GNA_ESTATE on a survival-chain plan.
  */
 gna_status gna_chain_eval_general(gna_plan* plan, const gna_osc_full* params, const double* eta, double sigma_eta,
                                   const double* data, int data_per_point, const gna_outputs* out, void* stream);

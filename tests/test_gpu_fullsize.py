@@ -129,3 +129,36 @@ def test_pseudo_data_full_size_sampled(api):
         assert np.array_equal(d[j].cpu().numpy(), ref), j
     m = d.mean(0).cpu().numpy()
     assert np.abs(m - case.mu_truth).max() < 6 * np.sqrt(case.mu_truth.max() / w.npts) + 1e-9
+
+
+def test_scan_numu_nue_full_sampled(api):
+    # the 64 x 64 scan for nu_mu -> nu_e appearance through the any-channel
+    # chain (s2_23 = 0.545, delta = 1.2 pi) on the 4096 uneven grids; sampled
+    # points against the oracle, with the tuning the autotuner picks
+    w = wl.scan_64x64_500bins()
+    k = w.npts
+    th6 = np.column_stack([w.theta[:, 0], w.theta[:, 1], np.full(k, 0.545), np.full(k, 1.2 * np.pi),
+                           w.theta[:, 2], w.theta[:, 3]])
+    truth = np.array([wl.TRUTH[0], wl.TRUTH[1], 0.545, 1.2 * np.pi, wl.TRUTH[2], wl.TRUTH[3]])
+    n_t = int(np.max(w.node_counts))
+    mu_rb, _ = oracle.binned_general(w.edges, n_t, w.L, truth, "mu", "e", False, w.e_scale)
+    N = 1e5 / mu_rb[0].sum()
+    data = wl.poisson_data(N * mu_rb[0], 13)
+    plan = api.Plan(w.edges, w.L, npts=k, node_counts=w.node_counts, norm=N, e_scale=w.e_scale, prec="ff",
+                    kind=w.kind, channel=("mu", "e", False))
+    p = plan.params_tensor(th6)
+    d = dev(data)
+    o = {"chi2": torch.empty(k, dtype=torch.float64, device="cuda"),
+         "grad": torch.empty(k, 6, dtype=torch.float64, device="cuda")}
+    plan.autotune(p, d, reps=1)
+    plan.eval_general(p, d, out=o)
+    torch.cuda.synchronize()
+    plan.status()
+    chi2 = o["chi2"].cpu().numpy()
+    g = o["grad"].cpu().numpy()
+    for q in [0, 1, 777, 2048, 4095, int(np.argmin(chi2))]:
+        ref = oracle.chain_general(w.edges, int(w.node_counts[q]), w.L, th6[q], N, data, "mu", "e", False, w.kind,
+                                   e_scale=w.e_scale)
+        assert abs(chi2[q] - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, data, w.kind), q
+        assert normrel(g[q], ref["grad"][:6]) < 1e-4, q
+    plan.close()

@@ -750,3 +750,24 @@ def test_general_plan_calls_and_status(api):
     gp.close()
     with pytest.raises(N.GnaError):  # FP64 is not offered for the any-channel chain
         api.Plan(edges, [810.0], nodes_per_bin=8, prec="fp64", channel=("mu", "e", False))
+
+
+@pytest.mark.parametrize("prec", ["ff", "f64phase"])
+def test_general_chain_per_point_data_and_chi2_only(api, prec):
+    # one data row per point, and chi^2 alone (no gradient: six node sums per
+    # bin instead of twelve), through the slice mapping
+    channel = ("mu", "e", False)
+    edges = np.linspace(500.0, 5000.0, 37)
+    theta, counts, N, data, eta, refs = general_case(channel, edges, 40, np.array([810.0]), 3, 1e-3, 1, 21)
+    rows = np.stack([wl.poisson_data(refs[p]["mu"], 30 + p) for p in range(3)])
+    plan = api.Plan(edges, [810.0], nodes_per_bin=40, npts=3, norm=N, e_scale=1e-3, prec=prec, kind="poisson",
+                    max_datasets=3, channel=channel)
+    out = plan.eval_general(plan.params_tensor(theta), dev(rows), grad=False, mu=True)
+    torch.cuda.synchronize()
+    plan.status()
+    assert "grad" not in out
+    for p in range(3):
+        ref = oracle.chain_general(edges, 40, [810.0], theta[p], N, rows[p], "mu", "e", False, 1, e_scale=1e-3)
+        assert abs(out["chi2"][p].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, rows[p], 1), p
+        assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < 1e-6, p
+    plan.close()

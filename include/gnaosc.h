@@ -7,7 +7,11 @@
  * one or more baselines, Pearson or Poisson chi^2 against data, the gradient
  * of chi^2 with respect to (sin^2 theta12, sin^2 theta13, dm2_21, dm2_32,
  * per-bin nuisances), batched parameter points with uneven grids, and batched
- * Levenberg-Marquardt fits.
+ * Levenberg-Marquardt fits.  The same chain for any channel P(alpha -> beta),
+ * neutrinos or antineutrinos, with the gradient in (sin^2 theta12,
+ * sin^2 theta13, sin^2 theta23, delta_cp, dm2_21, dm2_32); the element-wise
+ * probability for any channel, from device or pinned host memory; Poisson
+ * pseudo-data on the device.
  *
  * Paper: "CUDA Support in GNA Data Analysis Framework" (arXiv:1804.07682).
  * The probability is the paper's Sec. 4.1 vacuum formula with alpha = beta = e;
@@ -27,9 +31,11 @@
  *     argument errors are returned at once, device-side failures (CUDA
  *     errors, parameter points outside the physical domain) are reported by
  *     gna_plan_status().
- *   - Evaluation calls use only the memory gna_plan_create() allocated;
- *     the one call that allocates outside a plan is gna_gl_nodes (a
- *     temporary of 16 n bytes, freed before it returns).
+ *   - Evaluation calls use only the memory gna_plan_create() allocated.
+ *     Outside plans, gna_gl_nodes uses a temporary of 16 n bytes (freed
+ *     before it returns), gna_poisson_datasets a stream-ordered temporary,
+ *     and gna_oscprob_ee_staged keeps its staging buffers per device for the
+ *     life of the process.
  *   - No exception crosses the ABI.  Errors are gna_status codes; the text of
  *     the last error of a plan is gna_plan_error(plan).
  *   - Layouts are row-major C arrays; [a][b] means b varies fastest.
@@ -128,6 +134,8 @@ const char* gna_strerror(gna_status s);
  * weights), computed by a device kernel (Newton iteration on the Legendre
  * recurrence, FP64).  The rule is not in the paper; it is the integration
  * step of the chain.  x, w: device [n].  n in 1..65536 else GNA_ESHAPE.
+ * Synchronises `stream` before it returns (its 16 n-byte temporary is freed
+ * then).
  */
 gna_status gna_gl_nodes(int n, double* x, double* w, void* stream);
 

@@ -102,9 +102,10 @@ typedef struct {
                                    second kernel (default for uniform grids in the mixed
                                    precisions when points x bin groups are too few to fill the GPU) */
 #define GNA_PLAN_GENERAL 16     /* the chain for any channel (alpha, beta, anti above), evaluated by
-                                   gna_chain_eval_general: mixed precisions, up to 8 baselines, the
-                                   slice mapping on equal node counts and the bin mapping otherwise;
-                                   the survival-chain calls return GNA_ESTATE on such a plan */
+                                   gna_chain_eval_general: up to 8 baselines; in the mixed
+                                   precisions the slice mapping on equal node counts and the bin
+                                   mapping otherwise, in GNA_FP64 the bin mapping; the
+                                   survival-chain calls return GNA_ESTATE on such a plan */
 
 /* Outputs of one evaluation (device pointers; any may be NULL except chi2). */
 typedef struct {

@@ -185,8 +185,50 @@ static int resident_gen_ph(int nl, bool grad, int block) {
     return n > 0 ? n : 1;
 }
 
+static int resident_gen64(int nl, bool grad, int block) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (nl * 2 + (grad ? 1 : 0)) {
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<1, false>, block, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<1, true>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<2, false>, block, 0); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<2, true>, block, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<4, false>, block, 0); break;
+        case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<4, true>, block, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<8, false>, block, 0); break;
+        case 17: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused64_bins_gen<8, true>, block, 0); break;
+        default: break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 int general_resident_ctas(int ph, int nl, bool grad, int block) {
+    if (ph == 2) return resident_gen64(nl, grad, block);
     return ph == 0 ? resident_gen_ph<0>(nl, grad, block) : resident_gen_ph<1>(nl, grad, block);
+}
+
+template <int NL, bool GRAD>
+static cudaError_t launch_gen64(const GenArgs64& a, int grid, int block, cudaStream_t s) {
+    k_fused64_bins_gen<NL, GRAD><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_general64(int nl, bool grad, const GenArgs64& a, int grid, int block, cudaStream_t s) {
+    switch (nl * 2 + (grad ? 1 : 0)) {
+        case 2: return launch_gen64<1, false>(a, grid, block, s);
+        case 3: return launch_gen64<1, true>(a, grid, block, s);
+        case 4: return launch_gen64<2, false>(a, grid, block, s);
+        case 5: return launch_gen64<2, true>(a, grid, block, s);
+        case 8: return launch_gen64<4, false>(a, grid, block, s);
+        case 9: return launch_gen64<4, true>(a, grid, block, s);
+        case 16: return launch_gen64<8, false>(a, grid, block, s);
+        case 17: return launch_gen64<8, true>(a, grid, block, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t dispatch_general(int ph, int nl, bool grad, const GenArgs& a, int grid, int block, cudaStream_t s) {

@@ -25,6 +25,7 @@
 
 #include "epilogue.cuh"
 #include "fused.cuh"
+#include "fused64.cuh"
 
 namespace gna {
 
@@ -41,6 +42,11 @@ struct GenConst {
 
 struct GenArgs {
     BinArgs b;
+    const GenConst* gc;  // [npts]
+};
+
+struct GenArgs64 {
+    BinArgs64 b;
     const GenConst* gc;  // [npts]
 };
 
@@ -333,12 +339,140 @@ __global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __re
     }
 }
 
+// ------------------------------------------------------------- GNA_FP64 ----
+// The same sums with every step in double (phases reduced modulo pi in
+// double, CUDA's double sincos), for the bin mapping on the double grids
+// {1/E, W}.
+template <int NL, bool GRAD>
+struct NodeMathGen64 {
+    // the sums of the mixed variant, then sum_k W_k (the delta_ab term; the
+    // mixed precisions take it from the plan's per-bin weight sums)
+    static constexpr int NV = GRAD ? 13 : 7;
+    double c21[NL], c32[NL], om[NL], wk[NL];
+
+    __device__ __forceinline__ void load(const PointConst* pc, const BaseConst& bc) {
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            c21[r] = pc->c21[r];
+            c32[r] = pc->c32[r];
+            om[r] = bc.omd[r];
+            wk[r] = 2.0 * bc.omd[r] * bc.kld[r];
+        }
+    }
+
+    __device__ __forceinline__ void update(double2 g, double (&acc)[NV]) const {
+        const double e = g.x, W = g.y;
+        double U[3] = {0, 0, 0}, V[3] = {0, 0, 0}, Y[3] = {0, 0, 0}, Z[3] = {0, 0, 0};
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            double s1, c1, s2, c2;
+            sincos(reduce_pi_d(c21[r] * e), &s1, &c1);
+            sincos(reduce_pi_d(c32[r] * e), &s2, &c2);
+            const double s3 = s1 * c2 + c1 * s2, c3 = c1 * c2 - s1 * s2;
+            const double S[3] = {s1 * s1, s3 * s3, s2 * s2};
+            const double C[3] = {s1 * c1, s3 * c3, s2 * c2};
+            const double cc[3] = {c1, c3, c2};
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                U[j] += om[r] * S[j];
+                V[j] += om[r] * C[j];
+                if constexpr (GRAD) {
+                    Y[j] += wk[r] * C[j];
+                    Z[j] += wk[r] * (cc[j] * cc[j] - S[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            acc[j] += W * U[j];
+            acc[3 + j] += W * V[j];
+            if constexpr (GRAD) {
+                acc[6 + j] += W * e * Y[j];
+                acc[9 + j] += W * e * Z[j];
+            }
+        }
+        acc[NV - 1] += W;
+    }
+};
+
+// Epilogue of one bin with all sums and the contraction in double; v[nv - 1]
+// is the bin's sum of node weights.
+__device__ inline void gen_bin_epilogue64(const EpiArgs& a, const GenConst& c, int p, int i, const double* v,
+                                          int nv, const BinIn& in, float2* regs) {
+    const int64_t idx = (int64_t)p * a.nbins + i;
+    double M = c.dab * v[nv - 1];
+    for (int j = 0; j < 3; j++) M += c.a[j] * v[j] + c.b[j] * v[3 + j];
+    const double e = in.e;
+    const double f = a.norm * (1.0 + e);
+    const double mu = f * M;
+    const double d = in.d;
+    double term, gd;
+    if (a.kind == GNA_PEARSON) {
+        term = (d - mu) * (d - mu) / mu;
+        gd = 1.0 - (d * d) / (mu * mu);
+    } else {
+        term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
+        gd = 2.0 * (1.0 - d / mu);
+    }
+    const bool pen = a.eta && a.sigma > 0.0;
+    if (pen) term += e * e / (a.sigma * a.sigma);
+    regs[0] = to_ff(term);
+    if (a.has_grad) {
+        double dM[6];
+        for (int q = 0; q < 4; q++) {
+            dM[q] = 0.0;
+            for (int j = 0; j < 3; j++) dM[q] += c.da[q][j] * v[j] + c.db[q][j] * v[3 + j];
+        }
+        const double t31 = c.a[1] * v[7] + 0.5 * c.b[1] * v[10];
+        dM[4] = c.a[0] * v[6] + 0.5 * c.b[0] * v[9] + t31;
+        dM[5] = c.a[2] * v[8] + 0.5 * c.b[2] * v[11] + t31;
+        for (int q = 0; q < 6; q++) regs[1 + q] = to_ff(gd * f * dM[q]);
+    }
+    if (a.mu_out) a.mu_out[idx] = mu;
+    if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
+}
+
+template <int NL, bool GRAD>
+__global__ void __launch_bounds__(256) k_fused64_bins_gen(GenArgs64 ga) {
+    using M = NodeMathGen64<NL, GRAD>;
+    constexpr int NV = M::NV;
+    const BinArgs64& a = ga.b;
+    const int lane = threadIdx.x & 31;
+    int last_p = -1;
+    M m;
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.ntasks) break;
+        const int task = a.tasks[t];
+        const int p = task / a.ngroups;
+        const int b = task - p * a.ngroups;
+        const int gi = a.gid ? a.gid[p] : 0;
+        const int n = a.gn[gi];
+        if (p != last_p) {
+            m.load(a.pcs + p, a.bc);
+            last_p = p;
+        }
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) acc[v] = 0.0;
+        const double2* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
+        for (int k = 0; k < n; k++) m.update(g[(int64_t)k * 32], acc);
+        const int i = b * 32 + lane;
+        float2 regs[15];
+        if (i < a.nbins) gen_bin_epilogue64(a.ea, ga.gc[p], p, i, acc, NV, bin_inputs(a.ea, p, i), regs);
+        gen_group_done(a.ea, p, b, lane, regs);
+    }
+}
+
 // Launchers (general.cu).
 cudaError_t launch_prepare_general(const gna_osc_full* prm, int npts, const BaseConst& bc, int alpha, int beta,
                                    int anti, PointConst* out, GenConst* gout, int* zero, int64_t nz, int* status,
                                    cudaStream_t s);
 cudaError_t dispatch_general(int ph, int nl, bool grad, const GenArgs& a, int grid, int block, cudaStream_t s);
 int general_resident_ctas(int ph, int nl, bool grad, int block);
+cudaError_t dispatch_general64(int nl, bool grad, const GenArgs64& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_slices_reduce_general(const float2* part, int S, int NV, const EpiArgs& ea, const GenConst* gc,
                                          int npts, cudaStream_t s);
 

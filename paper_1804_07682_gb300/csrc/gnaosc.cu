@@ -855,7 +855,8 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     // groups alone do not (estimate: 16 resident warps per SM)
     const int64_t warps_est = 16LL * plan->sm_count;
     const bool slices_ok = plan->uniform && plan->ph < 2;
-    if (plan->general) plan->mapping = (plan->uniform && !(d->flags & GNA_PLAN_FORCE_BINS)) ? MAP_SLICES : MAP_BINS;
+    if (plan->general)
+        plan->mapping = (plan->uniform && plan->ph < 2 && !(d->flags & GNA_PLAN_FORCE_BINS)) ? MAP_SLICES : MAP_BINS;
     else if (d->flags & GNA_PLAN_FORCE_SPLIT) plan->mapping = MAP_SPLIT;
     else if (d->flags & GNA_PLAN_FORCE_BINS) plan->mapping = MAP_BINS;
     else if (d->flags & GNA_PLAN_FORCE_SLICES) plan->mapping = MAP_SLICES;
@@ -1060,7 +1061,7 @@ gna_status gna_plan_create(gna_plan** out, const gna_plan_desc* d, void* stream)
     }
     if (!(d->norm > 0.0)) return GNA_EINVAL;
     if (d->flags & GNA_PLAN_GENERAL) {
-        if (d->prec == GNA_FP64 || (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_WITH_PLAIN))) return GNA_EINVAL;
+        if (d->flags & (GNA_PLAN_FORCE_SPLIT | GNA_PLAN_WITH_PLAIN)) return GNA_EINVAL;
         if (d->alpha < 0 || d->alpha > 2 || d->beta < 0 || d->beta > 2 || (d->anti != 0 && d->anti != 1))
             return GNA_EINVAL;
         if (d->nL > 8) return GNA_ESHAPE;
@@ -1164,6 +1165,14 @@ gna_status gna_chain_eval_general(gna_plan* plan, const gna_osc_full* params, co
     const bool sliced = ssh.S > 1;
     int64_t g = (int64_t)plan->sm_count * general_resident_ctas(plan->ph, plan->nl_inst, grad, plan->block);
     g = std::max<int64_t>(1, std::min<int64_t>(g, ((int64_t)ssh.ntasks * 32 + plan->block - 1) / plan->block));
+    if (plan->ph == 2) {
+        GenArgs64 ga64{BinArgs64{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, plan->ntasks,
+                                 plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea},
+                       plan->d_gc};
+        CU(dispatch_general64(plan->nl_inst, grad, ga64, (int)g, plan->block, s));
+        plan->last_launches = 2;
+        return GNA_OK;
+    }
     GenArgs ga{BinArgs{plan->grid_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, ssh.ntasks,
                        plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, ssh.S, ssh.L,
                        sliced ? plan->d_slices : nullptr},

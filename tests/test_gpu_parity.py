@@ -675,21 +675,22 @@ def check_general(api, channel, prec, edges, counts, L, npts, e_scale, kind, see
                             0.02 if nuisances else 0.0, grad=True, grad_eta=nuisances, mu=True)
     torch.cuda.synchronize()
     plan.status()
-    # the FP32 rounding of sin^2 bounds the error of a node's P absolutely
-    # (~1e-7), so mu is held to 1e-6 relative plus 1e-7 of the bin's count at
-    # P = 1 (a disappearance dip turns the absolute bound into a larger
-    # relative one)
+    # mixed precisions: the FP32 rounding of sin^2 bounds the error of a
+    # node's P absolutely (~1e-7), so mu is held to 1e-6 relative plus 1e-7 of
+    # the bin's count at P = 1 (a disappearance dip turns the absolute bound
+    # into a larger relative one); GNA_FP64: 1e-9 relative, gradient 1e-9
+    tol, floor, gtol = (1e-9, 1e-13, 1e-9) if prec == "fp64" else (1e-6, 1e-7, 1e-4)
     L1 = np.atleast_1d(L)
     for p in range(npts):
         ref = refs[p]
         flat = oracle.baseline_weights(L1) @ oracle.binned(edges, int(counts[p]), L1, (0.3, 0.02, 0.0, 0.0), e_scale)
         scale = N * (1.0 + (0.0 if eta is None else eta)) * flat
-        assert abs(out["chi2"][p].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, data, kind), p
+        assert abs(out["chi2"][p].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, data, kind), p
         err = np.abs(out["mu"][p].cpu().numpy() - ref["mu"])
-        assert np.all(err <= 1e-6 * np.abs(ref["mu"]) + 1e-7 * scale), (p, float((err / ref["mu"]).max()))
-        assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:6]) < 1e-4, p
+        assert np.all(err <= tol * np.abs(ref["mu"]) + floor * scale), (p, float((err / ref["mu"]).max()))
+        assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:6]) < gtol, p
         if nuisances:
-            assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][6:]) < 1e-4, p
+            assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][6:]) < gtol, p
     plan.close()
 
 
@@ -698,7 +699,7 @@ CHANNELS = [("mu", "e", False), ("mu", "mu", False), ("mu", "e", True), ("e", "e
 
 
 @pytest.mark.parametrize("channel", CHANNELS)
-@pytest.mark.parametrize("prec", ["ff", "f64phase"])
+@pytest.mark.parametrize("prec", ["ff", "f64phase", "fp64"])
 def test_general_chain_long_baseline(api, channel, prec):
     # 810 km, 0.5-5 GeV (energies in MeV, spectrum in GeV), 3 points on one
     # grid of 40 bins x 24 nodes: the slice mapping
@@ -706,10 +707,11 @@ def test_general_chain_long_baseline(api, channel, prec):
 
 
 @pytest.mark.parametrize("channel", [("mu", "e", False), ("e", "e", True)])
-def test_general_chain_uneven_grids_baselines_nuisances(api, channel):
+@pytest.mark.parametrize("prec", ["ff", "fp64"])
+def test_general_chain_uneven_grids_baselines_nuisances(api, channel, prec):
     # per-point node counts (two points share one), three baselines (four-baseline
     # kernel with a zero-weight slot), Pearson chi^2 with nuisances: the bin mapping
-    check_general(api, channel, "ff", np.linspace(500.0, 5000.0, 71), [12, 30, 12, 7], np.array([810.0, 295.0, 1300.0]),
+    check_general(api, channel, prec, np.linspace(500.0, 5000.0, 71), [12, 30, 12, 7], np.array([810.0, 295.0, 1300.0]),
                   4, 1e-3, 0, 9, nuisances=True, uniform=False)
 
 
@@ -748,11 +750,9 @@ def test_general_plan_calls_and_status(api):
     ref = oracle.chain_general(edges, 8, [810.0], GEN_TH, 1.0, d.cpu().numpy(), "mu", "e", kind=0, e_scale=1e-3)
     assert rel(r["chi2"][0].item(), ref["chi2"]) < 1e-6
     gp.close()
-    with pytest.raises(N.GnaError):  # FP64 is not offered for the any-channel chain
-        api.Plan(edges, [810.0], nodes_per_bin=8, prec="fp64", channel=("mu", "e", False))
 
 
-@pytest.mark.parametrize("prec", ["ff", "f64phase"])
+@pytest.mark.parametrize("prec", ["ff", "f64phase", "fp64"])
 def test_general_chain_per_point_data_and_chi2_only(api, prec):
     # one data row per point, and chi^2 alone (no gradient: six node sums per
     # bin instead of twelve), through the slice mapping

@@ -60,9 +60,8 @@ def desc(N, **kw):
     (dict(norm=float("nan")), EINVAL),
     (dict(prec=3), EINVAL),
     (dict(kind=2), EINVAL),
-    # any-channel plans: mixed precisions, flavours 0..2, anti 0 or 1, up to 8
-    # baselines, no split mapping or plain chain
-    (dict(flags=16, prec=0), EINVAL),
+    # any-channel plans: flavours 0..2, anti 0 or 1, up to 8 baselines, no
+    # split mapping or plain chain
     (dict(flags=16, alpha=3), EINVAL),
     (dict(flags=16, beta=-1), EINVAL),
     (dict(flags=16, anti=2), EINVAL),

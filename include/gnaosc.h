@@ -289,6 +289,7 @@ gna_status gna_chain_eval(gna_plan* plan, const gna_osc* params, const double* e
  *   out:    chi2 [npts]; grad [npts][6] = d chi2 / d(s2_12, s2_13, s2_23,
  *           delta_cp, dm2_21, dm2_32) or NULL; grad_eta and mu as for
  *           gna_chain_eval; spectra must be NULL (GNA_EINVAL)
+ * Every precision of the plan is available (GNA_FP64 uses the bin mapping).
  * The node pass accumulates channel-free sums per bin (sin^2 and sin cos of
  * the three phases, and their derivatives in the phases); the epilogue
  * contracts them with the point's coefficients -4 Re X_ij, 4 Im X_ij and

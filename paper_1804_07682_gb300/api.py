@@ -483,7 +483,8 @@ def chi2_noalloc(E: torch.Tensor, W: torch.Tensor, L, params: torch.Tensor, data
 class OscChi2(torch.autograd.Function):
     """chi^2(theta, eta) of one plan point with its hand-written gradient.
 
-    forward runs one fused evaluation with the tangents on and keeps
+    theta has 4 parameters on a survival-chain plan and 6 on an any-channel
+    plan.  forward runs one fused evaluation with the tangents on and keeps
     d chi2 / d theta (and d chi2 / d eta); backward returns grad_output times
     the kept gradient.
     """
@@ -492,16 +493,19 @@ class OscChi2(torch.autograd.Function):
     def forward(ctx, theta, eta, plan: Plan, data, sigma: float = 0.0):
         if plan.npts != 1:
             raise ValueError("OscChi2 works on a single-point plan")
-        p = theta.detach().reshape(1, 4).contiguous()
+        npar = 4 if plan.channel is None else 6
+        p = theta.detach().reshape(1, npar).contiguous()
         e = None if eta is None else eta.detach().contiguous()
-        # the library writes chi2 and the whole gradient [4 (+ nbins)] straight
-        # into the tensors this call returns and keeps (no copies)
+        # the library writes chi2 and the whole gradient [npar (+ nbins)]
+        # straight into the tensors this call returns and keeps (no copies)
         chi2 = torch.empty((), dtype=torch.float64, device=p.device)
-        g = torch.empty(4 + (plan.nbins if e is not None else 0), dtype=torch.float64, device=p.device)
-        out = {"chi2": chi2, "grad": g[:4]}
+        g = torch.empty(npar + (plan.nbins if e is not None else 0), dtype=torch.float64, device=p.device)
+        out = {"chi2": chi2, "grad": g[:npar]}
         if e is not None:
-            out["grad_eta"] = g[4:]
-        plan.eval(p, data, e, sigma, grad=True, grad_eta=e is not None, out=out)
+            out["grad_eta"] = g[npar:]
+        ev = plan.eval if plan.channel is None else plan.eval_general
+        ev(p, data, e, sigma, grad=True, grad_eta=e is not None, out=out)
+        ctx.npar = npar
         ctx.save_for_backward(g)
         ctx.has_eta = e is not None
         ctx.shapes = (theta.shape, None if eta is None else eta.shape)
@@ -512,7 +516,8 @@ class OscChi2(torch.autograd.Function):
         (g,) = ctx.saved_tensors
         h = go * g
         ts, es = ctx.shapes
-        return h[:4].view(ts), (h[4:].view(es) if ctx.has_eta else None), None, None, None
+        k = ctx.npar
+        return h[:k].view(ts), (h[k:].view(es) if ctx.has_eta else None), None, None, None
 
 
 def chi2(theta, plan: Plan, data, eta=None, sigma: float = 0.0):

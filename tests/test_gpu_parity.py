@@ -771,3 +771,23 @@ def test_general_chain_per_point_data_and_chi2_only(api, prec):
         assert abs(out["chi2"][p].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, rows[p], 1), p
         assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < 1e-6, p
     plan.close()
+
+
+def test_general_chain_through_autograd(api):
+    # the autograd Function on an any-channel plan (GNA_FP64): the gradient in
+    # the six parameters and the nuisances against the oracle
+    channel = ("mu", "e", True)
+    edges = np.linspace(500.0, 5000.0, 25)
+    theta, counts, N, data, eta, refs = general_case(channel, edges, 16, np.array([810.0]), 1, 1e-3, 1, 41,
+                                                     nuisances=True)
+    plan = api.Plan(edges, [810.0], nodes_per_bin=16, norm=N, e_scale=1e-3, prec="fp64", kind="poisson",
+                    channel=channel)
+    th = dev(theta[0]).requires_grad_(True)
+    et = dev(eta).requires_grad_(True)
+    c = api.chi2(th, plan, dev(data), et, 0.02)
+    (3.0 * c).backward()
+    ref = refs[0]
+    assert rel(c.item(), ref["chi2"]) < 1e-9
+    assert normrel(th.grad.cpu().numpy(), 3.0 * ref["grad"][:6]) < 1e-9
+    assert normrel(et.grad.cpu().numpy(), 3.0 * ref["grad"][6:]) < 1e-9
+    plan.close()

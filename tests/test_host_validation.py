@@ -110,3 +110,9 @@ def test_pseudo_data_arguments(N):
         m2 = np.array([3.0, bad])
         assert f(m2.ctypes.data_as(DBL), 2, 5, 1, ctypes.c_void_p(8), None) == EINVAL
     assert f(mp, 2, 0, 1, None, None) == OK  # no data sets: validated, nothing drawn
+
+
+def test_any_channel_calls_without_a_plan(N):
+    o = N.GnaOutputs(None, None, None, None, None)
+    assert N.lib().gna_chain_eval_general(None, None, None, 0.0, None, 0, ctypes.byref(o), None) == EINVAL
+    assert N.lib().gna_plan_autotune_general(None, None, None, 0, ctypes.byref(o), 1, None) == EINVAL

@@ -243,9 +243,14 @@ def reference_arm(args):
 
 # -------------------------------------------------------------- side workloads --
 def side_workloads(api, torch, device, args):
-    """The batched workloads, each timed on its own after the main timed region:
-    the 64 x 64 scan (4096 points, uneven grids, one graph-replayed launch) and
-    the 16384 pseudo-experiment fits (20 Levenberg-Marquardt iterations)."""
+    """The other workloads, each timed on its own after the main timed region:
+    the 64 x 64 scan (4096 points, uneven grids, one graph-replayed launch),
+    the same scan for nu_mu -> nu_e through the any-channel chain, the 16384
+    pseudo-experiment fits (20 Levenberg-Marquardt iterations), the 10^4-node
+    reactor chain, the differentiable chi^2 with 1000 nuisances, OscProb
+    alone at the paper's Table 1 sizes (device, copies, staged, in place),
+    OscProb for any channel, and the device pseudo-data.  Returns the results
+    and the outputs the CPU-baseline leg checks against the oracle."""
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()

@@ -199,6 +199,11 @@ def reference_arm(args):
         return 0
     import oracle
 
+    if world > 1:
+        # the other ranks exit at once; the launcher's one-thread default is
+        # for N busy ranks, so this rank takes every host core
+        oracle.set_threads(os.cpu_count() or 1)
+
     w = wl.ALL[args.workload]()
     N = 1.0
     th = w.theta[0]

@@ -50,3 +50,20 @@ def test_two_replicas_report_max_time_and_total_throughput():
         assert ms == 150.0
         assert abs(rate - 2 * 20 / 0.150) < 1e-9
     assert out[0][3] != out[1][3]
+
+
+def test_reference_arm_under_two_ranks_prints_one_line():
+    # launched like the N > 1 runs: rank 0 alone times the oracle and prints
+    # the line; rank 1 exits 0 without work
+    import json
+    import subprocess
+
+    pytest.importorskip("torch")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(_free_port()), os.path.join(ROOT, "bench.py"), "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2 and lines[0]["value"] > 0

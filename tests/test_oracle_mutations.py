@@ -45,6 +45,9 @@ MUTATIONS = {
     "general_grad_product_rule_term": ("conj(V[a][i]) * V[b][i] * dV[q][a][j] * conj(V[b][j]) +\n", ""),
     "general_grad_im_term_dm": ("double dterm_dx = -4.0 * creal(X) * s2x + 4.0 * cimag(X) * c2x;",
                                 "double dterm_dx = -4.0 * creal(X) * s2x + 2.0 * cimag(X) * c2x;"),
+    "general_binned_baseline_index": ("prob_general_grad(alpha, beta, U, dU, osc6[4], osc6[5], L_km[r], E, anti, &P, dP);",
+                                      "prob_general_grad(alpha, beta, U, dU, osc6[4], osc6[5], L_km[0], E, anti, &P, dP);"),
+    "general_delta_ab_dropped": ("double p = (a == b) ? 1.0 : 0.0;", "double p = 0.0;"),
     "general_grad_dm32_chain": ("dP[5] += dterm_dx * dx * (dm2_d32[i] - dm2_d32[j]);",
                                 "dP[5] += dterm_dx * dx * (dm2_d21[i] - dm2_d21[j]);"),
 }

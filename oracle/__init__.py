@@ -11,8 +11,10 @@ differences and the Levenberg-Marquardt fit loop.
 
 Parity status of every function is pinned by ``tests/test_oracle_pins.py``
 (closed forms, amplitude brute force, library quadrature, erf integrals,
-finite differences) and ``tests/test_oracle_pseudo.py`` (the generator's
-known-answer vectors, the inversion's boundaries, the exact Poisson law);
+finite differences), ``tests/test_oracle_pseudo.py`` (the generator's
+known-answer vectors, the inversion's boundaries, the exact Poisson law) and
+``tests/test_oracle_fit_pins.py`` (the fitter's iterates on designed linear
+problems, derived by hand: the lambda schedule, rejections, ties, clamping);
 nothing here is "parity unpinned".
 """
 from __future__ import annotations

@@ -352,11 +352,15 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
 gna_status gna_chain_eval_host_wait(gna_plan* plan, int64_t ticket, double* chi2, double* grad, double* spectra);
 
 /* gna_chain_eval_plain: the same outputs computed by the plain FP64 chain,
- * one kernel per transformation as in the paper (OscProb and its tangents ->
- * weight -> bin integration -> chi^2), intermediates in device memory, CUDA's
- * double sin/cos.  Needs a plan created with GNA_PLAN_WITH_PLAIN and uniform
- * node counts (node_counts == NULL or all equal).  Points are processed one
- * after another.  The reference against which the fused path is measured. */
+ * one kernel per transformation as in the paper (Sec. 4.1: OscProb and its
+ * tangents -> weight -> bin integration -> chi^2), intermediates in device
+ * memory, CUDA's double sin/cos, no graph.  Needs a plan created with
+ * GNA_PLAN_WITH_PLAIN; any node counts, per-point data and nuisances.  The
+ * points are processed in chunks of at most 2^27 (point, baseline, node)
+ * elements (a point is never split), each chunk flattened over its points:
+ * 4 launches per chunk, 6 with a gradient.  The plan then also holds
+ * 40 bytes per chunk element of scratch and 16 bytes per energy node.  The
+ * reference against which the fused path is measured. */
 gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
                                 const double* data, int data_per_point, const gna_outputs* out, void* stream);
 
@@ -421,6 +425,15 @@ int gna_plan_kernel_launches(const gna_plan* plan);
 gna_status gna_plan_profile(gna_plan* plan, int on);
 gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches);
 
+/* gna_fp32_probe: a measurement aid, not a step of the chain (the paper has no
+ * counterpart): launches `blocks` blocks of 256 threads, each thread running 8
+ * independent FP32 FMA chains for `iters` steps, i.e. blocks x 2048 x iters
+ * FMAs, on `stream`.  Timed by the caller with events, it gives the FP32 pipe
+ * rate against which the node kernels' operation counts are compared.
+ * out: device [1] float, never written in practice (it keeps the work alive).
+ * GNA_EINVAL for out == NULL, blocks < 1 or iters < 1. */
+gna_status gna_fp32_probe(int blocks, int iters, float* out, void* stream);
+
 
 /* ---------------------------------------------------------------------------
  * gna_chain_eval_noalloc: chi^2 (and optionally its gradient and the binned
@@ -441,7 +454,13 @@ gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches
  *   chi2:   device [1]; grad: device [4] or NULL; mu: device [nbins] or NULL
  * Arithmetic as GNA_MIXED_FFPHASE.  Limits: nbins <= 2048, nL <= 8 and
  * nbins * ceil(n / 1024) <= 16384; beyond them the call returns GNA_ESHAPE
- * and launches nothing.  The first call on a device looks up the device
+ * and launches nothing.  GNA_EINVAL (nothing launched) for a NULL required
+ * pointer, a device pointer that is not global memory of the current device
+ * (or managed memory) or not aligned to 8 bytes, norm <= 0, an unknown chi^2
+ * kind, L <= 0 or a negative weight.  The parameters live on the device and
+ * are not range-checked by this call (there is no status word to report
+ * through): a point outside the physical domain (s2 outside [0, 1], a mass
+ * splitting not finite) gives a meaningless chi^2.  The first call on a device looks up the device
  * address of the array (cudaGetSymbolAddress) once for that device; make that
  * first call before any stream capture on the device.  Each call clears the
  * counters it needs; the rest of the array keeps the previous call's

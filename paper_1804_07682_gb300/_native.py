@@ -99,6 +99,7 @@ SIGNATURES = {
     "gna_plan_kernel_launches": (c_int, [c_void_p]),
     "gna_plan_profile": (c_int, [c_void_p, c_int]),
     "gna_plan_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
+    "gna_fp32_probe": (c_int, [c_int, c_int, c_void_p, c_void_p]),
     "gna_chain_eval_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, ctypes.POINTER(c_double), c_int,
                                        ctypes.POINTER(c_double), c_void_p, c_double, c_int, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p]),

@@ -167,6 +167,17 @@ def poisson_datasets(mu, ndatasets: int, seed: int, stream=None) -> torch.Tensor
     return out
 
 
+def fp32_probe(blocks: int, iters: int, out: Optional[torch.Tensor] = None, stream=None) -> int:
+    """Enqueues the FP32 FMA-rate probe (blocks x 256 threads, 8 chains of
+    iters FMAs each) on the current stream; returns the FMAs it executes."""
+    _require_cuda()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float32, device="cuda")
+    N.check(N.lib().gna_fp32_probe(int(blocks), int(iters), _ptr(out), ctypes.c_void_p(_stream(stream))),
+            what="gna_fp32_probe")
+    return int(blocks) * 256 * 8 * int(iters)
+
+
 class Plan:
     """A configured chain (paper's configuration stage): energy grids built and
     all scratch allocated on the device; evaluations only launch kernels."""
@@ -448,6 +459,41 @@ class Plan:
         return self.tuning
 
 
+def _check_noalloc_args(E, W, Ls, Lw, params, data, out):
+    """Refuses, before anything reaches the library, every argument of
+    chi2_noalloc whose dtype, shape or device would make the kernels read or
+    write outside the caller's buffers: dtypes and shapes first, then that all
+    tensors are contiguous CUDA tensors on E's device."""
+    f64 = torch.float64
+    if not isinstance(E, torch.Tensor) or E.dtype != f64 or E.dim() != 2:
+        raise ValueError("E must be a float64 tensor [nbins, n]")
+    nbins = E.shape[0]
+    if not isinstance(W, torch.Tensor) or W.dtype != f64 or tuple(W.shape) != tuple(E.shape):
+        raise ValueError("W must be a float64 tensor shaped like E %s" % (tuple(E.shape),))
+    if not isinstance(params, torch.Tensor) or params.dtype != f64 or params.numel() != 4:
+        raise ValueError("params must be a float64 tensor of 4 values [1, 4]")
+    if not isinstance(data, torch.Tensor) or data.dtype != f64 or data.numel() != nbins:
+        raise ValueError("data must be a float64 tensor of nbins = %d values" % nbins)
+    if Ls.ndim != 1 or Ls.size < 1 or (Lw is not None and Lw.shape != Ls.shape):
+        raise ValueError("L must hold one or more baselines and Lweight (if given) one weight per baseline")
+    tensors = [E, W, params, data]
+    if out is not None:
+        need = {"chi2": 1, "grad": 4, "mu": nbins}
+        if "chi2" not in out:
+            raise ValueError("out must hold 'chi2'")
+        for k, t in out.items():
+            if k not in need:
+                raise ValueError("unknown output %r" % k)
+            if not isinstance(t, torch.Tensor) or t.dtype != f64 or t.numel() < need[k]:
+                raise ValueError("out[%r] must be a float64 tensor of at least %d values" % (k, need[k]))
+            tensors.append(t)
+    for t in tensors:
+        if not t.is_cuda or t.device != E.device:
+            raise ValueError("all tensors must be CUDA tensors on E's device")
+        if not t.is_contiguous():
+            raise ValueError("all tensors must be contiguous")
+
+
 def chi2_noalloc(E: torch.Tensor, W: torch.Tensor, L, params: torch.Tensor, data: torch.Tensor, norm: float,
                  kind="pearson", Lweight=None, grad: bool = True, mu: bool = False, out: Optional[dict] = None,
                  stream=None) -> dict:
@@ -461,10 +507,11 @@ def chi2_noalloc(E: torch.Tensor, W: torch.Tensor, L, params: torch.Tensor, data
     ``out`` (chi2 [1], grad [4], mu [nbins]) so that this call allocates
     nothing on the Python side either.
     """
-    _require_cuda()
-    nbins, n = E.shape
     Ls = _f64(np.atleast_1d(L))
     Lw = None if Lweight is None else _f64(Lweight)
+    _check_noalloc_args(E, W, Ls, Lw, params, data, out)
+    _require_cuda()
+    nbins, n = E.shape
     if out is None:
         out = {"chi2": torch.empty(1, dtype=torch.float64, device=E.device)}
         if grad:

@@ -131,6 +131,9 @@ __global__ void k_prepare_general(const gna_osc_full* __restrict__ prm, int npts
                         o.s2_23 < 1.0 && isfinite(o.delta_cp) && isfinite(o.dm2_21) && isfinite(o.dm2_32);
     if (!inside && status) atomicExch(status, (int)GNA_EINVAL);
     general_coefficients(o, alpha, beta, anti, gout[p]);
+    double w = 0.0;
+    for (int q = 0; q < bc.nL; q++) w += (double)bc.om[q] + (double)bc.omlo[q];
+    gout[p].wsum = w;
 }
 
 cudaError_t launch_prepare_general(const gna_osc_full* prm, int npts, const BaseConst& bc, int alpha, int beta,
@@ -240,7 +243,7 @@ cudaError_t dispatch_general(int ph, int nl, bool grad, const GenArgs& a, int gr
 cudaError_t launch_slices_reduce_general(const float2* part, int S, int NV, const EpiArgs& ea, const GenConst* gc,
                                          int npts, cudaStream_t s) {
     constexpr int W = 24;
-    if (NV < 1 || NV > 12) return cudaErrorInvalidValue;
+    if (NV != gen_nv(false) && NV != gen_nv(true)) return cudaErrorInvalidValue;
     static std::once_flag once[64];
     static cudaError_t attr[64];
     int dev = 0;
@@ -249,7 +252,7 @@ cudaError_t launch_slices_reduce_general(const float2* part, int S, int NV, cons
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::call_once(once[dev], [&] {
         attr[dev] = cudaFuncSetAttribute(k_slices_reduce_gen<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float2) * W * 12 * 32 + sizeof(double) * 12 * 32));
+                                         (int)(sizeof(float2) * W * gen_nv(true) * 32 + sizeof(double) * gen_nv(true) * 32));
     });
     if (attr[dev] != cudaSuccess) return attr[dev];
     cudaLaunchConfig_t cfg{};

@@ -18,6 +18,16 @@
 //   dM/d dm2_21 = sum_{ij = 21, 31} (a_ij Y_ij + b_ij Z_ij / 2),
 //   dM/d dm2_32 = sum_{ij = 32, 31} (a_ij Y_ij + b_ij Z_ij / 2)
 // (d S / dx = 2 C, d C / dx = cos^2 - sin^2, dx/d dm2 = K L / E).
+//
+// Survival channels cancel: P = 1 + sum a S with a = -4 |V_ai|^2 |V_aj|^2 of
+// order -1, so where S -> 1 (a disappearance dip) M is a small difference of
+// sum W and a U, and the FP32 rounding of S near 1 (~6e-8 absolute per node)
+// becomes a large relative error of M.  The mixed node pass therefore also
+// accumulates Q_ij = sum_k W_k sum_r omega_r cos^2 x_ij, and the epilogue takes
+// each pair's sine sum either as U_ij or, when Q_ij < U_ij, as
+// sum_k W_k sum_r omega_r - Q_ij (sin^2 + cos^2 = 1, applied in double): both
+// sums add positive terms, so the one used carries an error relative to the
+// smaller of the two, which is small wherever P dips.
 // These kernels reuse the energy-grid layouts, the bin/slice task scheme and
 // the group and point reductions of the nue_bar survival chain; they are
 // separate kernels so that the survival chain's code stays as it is.
@@ -38,7 +48,12 @@ struct GenConst {
     // FP32 copies for the gradient terms (FP64 instructions run at 1/64 of
     // the FP32 rate on this part; the gradient is held to 1e-4)
     float af[3], bf[3], daf[4][3], dbf[4][3];
+    // sum_r omega_r as the mixed node pass applies the FP32 weights (hi + lo)
+    double wsum;
 };
+
+// Values per (point, bin) of the mixed node pass: U(3), V(3), [Y(3), Z(3)], Q(3).
+__host__ __device__ constexpr int gen_nv(bool grad) { return grad ? 15 : 9; }
 
 struct GenArgs {
     BinArgs b;
@@ -50,9 +65,49 @@ struct GenArgs64 {
     const GenConst* gc;  // [npts]
 };
 
+// Phase c * e (double-float) reduced modulo pi/2: phase = q pi/2 + r with
+// |r| <= pi/4 (+ rounding); returns r and whether q is odd (bit 0 of the
+// magic-rounded quotient).  pi/2 = (PI_A + PI_B + PI_C) / 2 with 12-bit PI_A
+// and PI_B: for q < 2^12 (phases below 6434 rad) q PI_A / 2 and q PI_B / 2 are
+// exact, so is r1 - q PI_B / 2, and r is rounded once, when the small part
+// lo - q PI_C / 2 is added.  With |r| <= pi/4 neither polynomial cancels:
+// cos x near a zero of cos is evaluated as a sine of a small r, to a relative
+// error of a few ulp (near r = pi/2, 1 + u cos_tail(u) loses ~1e-7 absolute).
+__device__ __forceinline__ float reduce_pi2_ff(float ch, float cl, float eh, float el, bool& odd) {
+    const float p = __fmul_rn(ch, eh);
+    const float e = __fmaf_rn(ch, eh, -p);
+    const float lo = __fmaf_rn(ch, el, __fmaf_rn(cl, eh, e));
+    const float qm = __fmaf_rn(p, 2.0f * GNA_INV_PI_F, GNA_ROUND_MAGIC);
+    odd = (__float_as_uint(qm) & 1u) != 0u;
+    const float q = __fsub_rn(qm, GNA_ROUND_MAGIC);
+    float r = __fmaf_rn(-q, 0.5f * GNA_PI_A, p);
+    r = __fmaf_rn(-q, 0.5f * GNA_PI_B, r);
+    return __fadd_rn(r, __fmaf_rn(-q, 0.5f * GNA_PI_C, lo));
+}
+
+// The same with the phase formed and reduced in double (1.5 2^52 rounds to an integer).
+__device__ __forceinline__ float reduce_pi2_f64(double c, double e, bool& odd) {
+    const double p = c * e;
+    const double qm = fma(p, 2.0 * GNA_INV_PI_D, 6755399441055744.0);
+    odd = (__double2loint(qm) & 1) != 0;
+    const double q = qm - 6755399441055744.0;
+    double r = fma(-q, 0.5 * GNA_PI_DA, p);
+    r = fma(-q, 0.5 * GNA_PI_DB, r);
+    return (float)fma(-q, 0.5 * GNA_PI_DC, r);
+}
+
+// (sin x, cos x) up to a common sign (which sin^2, cos^2 and sin cos do not
+// see) from x = q pi/2 + r: (sin r, cos r) for even q, (cos r, -sin r) for odd q.
+__device__ __forceinline__ void sincos_quadrant(float r, bool odd, float& s, float& c) {
+    float sr, cr;
+    sincos_poly(r, sr, cr);
+    s = odd ? cr : sr;
+    c = odd ? -sr : cr;
+}
+
 template <int PH, int NL, bool GRAD>
 struct NodeMathGen {
-    static constexpr int NV = GRAD ? 12 : 6;
+    static constexpr int NV = gen_nv(GRAD);
     // with several baselines the weights enter as hi + lo (no bias from the
     // FP32 rounding of omega_r)
     static constexpr bool LO = NL > 1;
@@ -75,21 +130,22 @@ struct NodeMathGen {
         const float eh = g.x, el = g.y, W = g.z, We = g.w;
         double ed = 0.0;
         if (PH == 1) ed = (double)eh + (double)el;
-        float U[3] = {0.f, 0.f, 0.f}, V[3] = {0.f, 0.f, 0.f};
+        float U[3] = {0.f, 0.f, 0.f}, V[3] = {0.f, 0.f, 0.f}, Q[3] = {0.f, 0.f, 0.f};
         float Y[3] = {0.f, 0.f, 0.f}, Z[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int r = 0; r < NL; r++) {
             float s1, c1, s2, c2;
             float r21, r32;
+            bool o21, o32;
             if (PH == 0) {
-                r21 = reduce_pi_ff(ph.ch21[r], ph.cl21[r], eh, el);
-                r32 = reduce_pi_ff(ph.ch32[r], ph.cl32[r], eh, el);
+                r21 = reduce_pi2_ff(ph.ch21[r], ph.cl21[r], eh, el, o21);
+                r32 = reduce_pi2_ff(ph.ch32[r], ph.cl32[r], eh, el, o32);
             } else {
-                r21 = reduce_pi_f64(ph.cd21[r], ed);
-                r32 = reduce_pi_f64(ph.cd32[r], ed);
+                r21 = reduce_pi2_f64(ph.cd21[r], ed, o21);
+                r32 = reduce_pi2_f64(ph.cd32[r], ed, o32);
             }
-            sincos_poly(r21, s1, c1);
-            sincos_poly(r32, s2, c2);
+            sincos_quadrant(r21, o21, s1, c1);
+            sincos_quadrant(r32, o32, s2, c2);
             // x31 = x21 + x32 up to a multiple of pi: sin^2, sin cos and
             // cos^2 - sin^2 do not see it
             const float s3 = fmaf(s1, c2, c1 * s2);
@@ -97,13 +153,16 @@ struct NodeMathGen {
             const float S[3] = {s1 * s1, s3 * s3, s2 * s2};
             const float C[3] = {s1 * c1, s3 * c3, s2 * c2};
             const float cc[3] = {c1, c3, c2};
+            const float Cs[3] = {c1 * c1, c3 * c3, c2 * c2};
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 U[j] = fmaf(om[r], S[j], U[j]);
                 V[j] = fmaf(om[r], C[j], V[j]);
+                Q[j] = fmaf(om[r], Cs[j], Q[j]);
                 if constexpr (LO) {
                     U[j] = fmaf(omlo[r], S[j], U[j]);
                     V[j] = fmaf(omlo[r], C[j], V[j]);
+                    Q[j] = fmaf(omlo[r], Cs[j], Q[j]);
                 }
                 if constexpr (GRAD) {
                     Y[j] = fmaf(wkl[r], C[j], Y[j]);
@@ -119,20 +178,29 @@ struct NodeMathGen {
                 kadd_prod(acc[6 + j], We, Y[j]);
                 kadd_prod(acc[9 + j], We, Z[j]);
             }
+            kadd_prod(acc[NV - 3 + j], W, Q[j]);
         }
     }
 };
 
-// Bin i of point p from its summed values [U(3), V(3)] (+ [Y(3), Z(3)]):
-// vd the first six in double, vf all of them in FP32, and the point's
-// coefficients: M in double (its terms may cancel), its six derivatives in
-// FP32, then the chi^2 term and its gradient contributions into
-// regs[0..6] (float pairs): [0] the chi^2 term, [1 + q] g_i N (1 + eta_i) dM/dp_q.
+// Bin i of point p from its summed values [U(3), V(3)] (+ [Y(3), Z(3)]) and
+// Q(3): vd = {U, V, Q} (nine values) in double, vf the NV values in FP32, and
+// the point's coefficients.  Each pair's sine sum is U, or sum W sum omega - Q
+// where Q is the smaller sum (see the header); M is formed in double (its
+// terms may cancel), its six derivatives in FP32, then the chi^2 term and its
+// gradient contributions into regs[0..6] (float pairs): [0] the chi^2 term,
+// [1 + q] g_i N (1 + eta_i) dM/dp_q.
 __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int p, int i, const double* vd,
                                         const float* vf, const BinIn& in, float2* regs) {
     const int64_t idx = (int64_t)p * a.nbins + i;
     double M = c.dab * in.sumw;
-    for (int j = 0; j < 3; j++) M += c.a[j] * vd[j] + c.b[j] * vd[3 + j];
+    const double wtot = in.sumw * c.wsum;
+    float Sf[3];
+    for (int j = 0; j < 3; j++) {
+        const double Sj = (vd[6 + j] < vd[j]) ? wtot - vd[6 + j] : vd[j];
+        Sf[j] = (float)Sj;
+        M += c.a[j] * Sj + c.b[j] * vd[3 + j];
+    }
     const double e = in.e;
     const double f = a.norm * (1.0 + e);
     const double mu = f * M;
@@ -152,7 +220,7 @@ __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int
         float dM[6];
         for (int q = 0; q < 4; q++) {
             dM[q] = 0.f;
-            for (int j = 0; j < 3; j++) dM[q] = fmaf(c.daf[q][j], vf[j], fmaf(c.dbf[q][j], vf[3 + j], dM[q]));
+            for (int j = 0; j < 3; j++) dM[q] = fmaf(c.daf[q][j], Sf[j], fmaf(c.dbf[q][j], vf[3 + j], dM[q]));
         }
         // pairs 0 = 21, 1 = 31, 2 = 32; x31 moves with both splittings
         const float t31 = fmaf(c.af[1], vf[7], 0.5f * c.bf[1] * vf[10]);
@@ -269,10 +337,13 @@ __global__ void __launch_bounds__(256) k_fused_bins_gen(GenArgs ga) {
         const int i = b * 32 + lane;
         float2 regs[15];
         if (i < a.nbins) {
-            double vd[6];
-            float vf[12];
+            double vd[9];
+            float vf[NV];
 #pragma unroll
-            for (int j = 0; j < 6; j++) vd[j] = (double)acc[j].s - (double)acc[j].c;
+            for (int j = 0; j < 9; j++) {
+                const int v = j < 6 ? j : NV - 9 + j;  // U, V, then Q
+                vd[j] = (double)acc[v].s - (double)acc[v].c;
+            }
 #pragma unroll
             for (int j = 0; j < NV; j++) vf[j] = acc[j].s - acc[j].c;
             gen_bin_epilogue(a.ea, ga.gc[p], p, i, vd, vf, bin_inputs(a.ea, p, i), regs);
@@ -282,13 +353,13 @@ __global__ void __launch_bounds__(256) k_fused_bins_gen(GenArgs ga) {
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-// Slice sums of the general channel (NV <= 12 values), in slice order, then
-// the epilogue and the group and point reductions: k_slices_reduce with the
-// general epilogue.
+// Slice sums of the general channel (NV = 9 or 15 values), in slice order,
+// then the epilogue and the group and point reductions: k_slices_reduce with
+// the general epilogue.
 template <int W>
 __global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __restrict__ part, int S, int NV,
                                                                EpiArgs ea, const GenConst* __restrict__ gc) {
-    constexpr int NVM = 12;
+    constexpr int NVM = gen_nv(true);
     extern __shared__ float2 red[];  // [W][NV][32], then [NV][32] doubles
     double* fin = reinterpret_cast<double*>(red + W * NV * 32);
     const int pg = blockIdx.x;
@@ -326,12 +397,13 @@ __global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __re
     }
     __syncthreads();
     if (w == 0) {
-        double vd[6];
+        double vd[9];
         float vf[NVM];
         for (int v = 0; v < NV; v++) {
             const float2 t = fin2[v * 32 + lane];
             vf[v] = t.x + t.y;
             if (v < 6) vd[v] = (double)t.x + (double)t.y;
+            else if (v >= NV - 3) vd[v - NV + 9] = (double)t.x + (double)t.y;  // Q
         }
         float2 regs[15];
         if (i < ea.nbins) gen_bin_epilogue(ea, gc[p], p, i, vd, vf, in, regs);

@@ -134,7 +134,12 @@ struct gna_plan {
     double* d_H = nullptr;
     double* d_chi2_tmp = nullptr;
     double* d_grad_tmp = nullptr;
-    // plain chain scratch
+    // plain chain: element offsets per point, grid offsets, chunks of points
+    // (first point of each chunk, then npts), scratch for one chunk
+    std::vector<int64_t> plain_off;
+    std::vector<int> plain_chunks;
+    int64_t* d_plain_off = nullptr;
+    int64_t* d_plain_goff = nullptr;
     double* d_plainP = nullptr;
     double* d_plainD = nullptr;
     double* d_plainMu = nullptr;
@@ -901,7 +906,6 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         for (int p = 0; p < d->npts; p++) plan->total_nodes += (int64_t)d->nbins * plan->counts[p];
     const bool want64 = plan->ph == 2;
     const bool want_plain = (d->flags & GNA_PLAN_WITH_PLAIN) != 0;
-    if (want_plain && !plan->uniform) return fail(plan, GNA_EINVAL, "the plain chain needs equal node counts");
     TRY(dalloc(plan, &plan->d_edges, d->nbins + 1));
     CU(cudaMemcpyAsync(plan->d_edges, d->edges, sizeof(double) * (d->nbins + 1), cudaMemcpyHostToDevice, s));
     if (plan->has_split) {
@@ -912,8 +916,16 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         if (plan->ph < 2) TRY(dalloc(plan, &plan->grid_bins, len_bins));
         if (want64) TRY(dalloc(plan, &plan->grid64_bins, len_bins));
     }
+    // plain chain: one bin-major {1/E, W} grid per distinct node count (the
+    // FP64 split grid when the plan has one: the same layout)
     const bool plain_alias = want_plain && plan->grid64_split;
-    if (want_plain && !plain_alias) TRY(dalloc(plan, &plan->plain64, (size_t)d->nbins * plan->n_uniform));
+    std::vector<int64_t> plain_goff(plan->ngrids);
+    int64_t plain_len = 0;
+    for (int g = 0; g < plan->ngrids; g++) {
+        plain_goff[g] = plain_len;
+        plain_len += (int64_t)d->nbins * gn[g];
+    }
+    if (want_plain && !plain_alias) TRY(dalloc(plan, &plan->plain64, plain_len));
     TRY(dalloc(plan, &plan->d_goff, plan->ngrids));
     TRY(dalloc(plan, &plan->d_gn, plan->ngrids));
     CU(cudaMemcpyAsync(plan->d_goff, goff.data(), sizeof(int64_t) * plan->ngrids, cudaMemcpyHostToDevice, s));
@@ -951,7 +963,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
             CU(launch_build_grid(d->nbins, nbins_pad, plan->d_edges, n, glx + gl_off[n], glw + gl_off[n],
                                  plan->e_scale, 1, plan->grid_bins ? plan->grid_bins + goff[g] : nullptr,
                                  plan->grid64_bins ? plan->grid64_bins + goff[g] : nullptr,
-                                 (g == 0 && !plan->has_split) ? plan->plain64 : nullptr, s));
+                                 (plan->plain64 && !plan->has_split) ? plan->plain64 + plain_goff[g] : nullptr, s));
         }
     if (plain_alias) plan->plain64 = plan->grid64_split;
     if (plan->ph < 2) {
@@ -983,7 +995,7 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     // scratch
     TRY(dalloc(plan, &plan->d_pc, d->npts));
     if (plan->general) TRY(dalloc(plan, &plan->d_gc, d->npts));
-    const int nv_max = std::max(fused_nv(plan->nl_inst, true, true), plan->general ? 12 : 0);
+    const int nv_max = std::max(fused_nv(plan->nl_inst, true, true), plan->general ? gen_nv(true) : 0);
     if (plan->has_split) {
         // ranges are at least 128 nodes long, so a bin meets at most ceil(n / 128) + 1 of
         // them; the slot count is capped so that the partials stay within 256 M values
@@ -1031,11 +1043,35 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
     TRY(dalloc(plan, &plan->d_status, 1));
     CU(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
     if (want_plain) {
-        const size_t nn = (size_t)d->nbins * plan->n_uniform;
-        TRY(dalloc(plan, &plan->d_plainP, nn * d->nL));
-        TRY(dalloc(plan, &plan->d_plainD, 4 * nn * d->nL));
-        TRY(dalloc(plan, &plan->d_plainMu, (size_t)d->nL * d->nbins));
-        TRY(dalloc(plan, &plan->d_plainDmu, 4 * (size_t)d->nL * d->nbins));
+        // points in chunks of at most 2^27 (point, baseline, node) elements
+        // (P 1 GB, tangents 4 GB), a point never split across chunks
+        std::vector<int64_t>& off = plan->plain_off;
+        off.assign(d->npts + 1, 0);
+        int64_t max_pt = 0;
+        for (int p = 0; p < d->npts; p++) {
+            off[p + 1] = off[p] + (int64_t)d->nbins * plan->counts[p] * d->nL;
+            max_pt = std::max(max_pt, off[p + 1] - off[p]);
+        }
+        const int64_t cap = std::max(max_pt, std::min<int64_t>(1LL << 27, off[d->npts]));
+        plan->plain_chunks.clear();
+        int max_cnt = 0;
+        for (int p = 0; p < d->npts;) {
+            int q = p + 1;
+            while (q < d->npts && off[q + 1] - off[p] <= cap) q++;
+            plan->plain_chunks.push_back(p);
+            max_cnt = std::max(max_cnt, q - p);
+            p = q;
+        }
+        plan->plain_chunks.push_back(d->npts);
+        TRY(dalloc(plan, &plan->d_plain_off, off.size()));
+        CU(cudaMemcpyAsync(plan->d_plain_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
+        TRY(dalloc(plan, &plan->d_plain_goff, plain_goff.size()));
+        CU(cudaMemcpyAsync(plan->d_plain_goff, plain_goff.data(), sizeof(int64_t) * plain_goff.size(),
+                           cudaMemcpyHostToDevice, s));
+        TRY(dalloc(plan, &plan->d_plainP, cap));
+        TRY(dalloc(plan, &plan->d_plainD, 4 * cap));
+        TRY(dalloc(plan, &plan->d_plainMu, (size_t)max_cnt * d->nL * d->nbins));
+        TRY(dalloc(plan, &plan->d_plainDmu, 4 * (size_t)max_cnt * d->nL * d->nbins));
     }
     CU(cudaStreamSynchronize(s));
     CU(cudaGetLastError());
@@ -1148,7 +1184,7 @@ gna_status gna_chain_eval_general(gna_plan* plan, const gna_osc_full* params, co
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     const bool grad = out->grad || out->grad_eta;
-    const int NV = grad ? 12 : 6;
+    const int NV = gen_nv(grad);
     SliceShape ssh{1, 0, plan->ntasks};
     if (plan->mapping == MAP_SLICES) {
         ssh = slice_shape(plan);
@@ -1339,25 +1375,46 @@ gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const dou
     const bool grad = out->grad || out->grad_eta;
     CU(launch_prepare(params, plan->npts, plan->bc, plan->d_pc, s, nullptr, 0, plan->d_status));
     int nl = 1;
-    for (int p = 0; p < plan->npts; p++) {
+    for (size_t c = 0; c + 1 < plan->plain_chunks.size(); c++) {
+        const int p0 = plan->plain_chunks[c], p1 = plan->plain_chunks[c + 1];
+        PlainArgs a{};
+        a.nodes = plan->plain64;
+        a.goff = plan->d_plain_goff;
+        a.gn = plan->d_gn;
+        a.gid = plan->d_gid;
+        a.off = plan->d_plain_off;
+        a.pcs = plan->d_pc;
+        a.bc = plan->bc;
+        a.nbins = plan->nbins;
+        a.nL = plan->nL;
+        a.p0 = p0;
+        a.cnt = p1 - p0;
+        a.grad = grad;
+        a.len = plan->plain_off[p1] - plan->plain_off[p0];
+        a.P = plan->d_plainP;
+        a.dP = plan->d_plainD;
+        a.mu_r = plan->d_plainMu;
+        a.dmu = plan->d_plainDmu;
         PlainChi2Args ca{};
         ca.mu_r = plan->d_plainMu;
         ca.dmu = grad ? plan->d_plainDmu : nullptr;
         ca.bc = plan->bc;
         ca.nL = plan->nL;
         ca.nbins = plan->nbins;
+        ca.p0 = p0;
+        ca.cnt = p1 - p0;
         ca.norm = plan->norm;
         ca.kind = plan->kind;
         ca.eta = eta;
         ca.sigma = sigma_eta;
-        ca.data = data + (data_per_point ? (size_t)p * plan->nbins : 0);
-        ca.chi2 = out->chi2 + p;
-        ca.grad = out->grad ? out->grad + 4 * (size_t)p : nullptr;
-        ca.mu_out = out->mu ? out->mu + (size_t)p * plan->nbins : nullptr;
-        ca.grad_eta_out = out->grad_eta ? out->grad_eta + (size_t)p * plan->nbins : nullptr;
-        ca.spectra_out = out->spectra ? out->spectra + (size_t)p * plan->nL * plan->nbins : nullptr;
-        CU(launch_plain_point(plan->plain64, plan->nbins, plan->n_uniform, plan->d_pc + p, plan->bc, plan->nL, grad,
-                              plan->d_plainP, plan->d_plainD, plan->d_plainMu, plan->d_plainDmu, ca, s));
+        ca.data = data;
+        ca.dpp = data_per_point;
+        ca.chi2 = out->chi2;
+        ca.grad = out->grad;
+        ca.mu_out = out->mu;
+        ca.grad_eta_out = out->grad_eta;
+        ca.spectra_out = out->spectra;
+        CU(launch_plain_chunk(a, ca, s));
         nl += grad ? 6 : 4;
     }
     plan->last_launches = nl;
@@ -1572,6 +1629,11 @@ gna_status gna_plan_set_graph(gna_plan* plan, int on) {
 }
 
 int gna_plan_kernel_launches(const gna_plan* plan) { return plan ? plan->last_launches : 0; }
+
+gna_status gna_fp32_probe(int blocks, int iters, float* out, void* stream) {
+    if (!out || blocks < 1 || iters < 1) return GNA_EINVAL;
+    return launch_fma_probe(blocks, iters, out, (cudaStream_t)stream) == cudaSuccess ? GNA_OK : GNA_ECUDA;
+}
 
 gna_status gna_plan_profile(gna_plan* plan, int on) {
     if (!plan) return GNA_EINVAL;

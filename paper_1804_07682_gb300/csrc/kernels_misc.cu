@@ -200,66 +200,105 @@ cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int
 // ------------------------------------------------- plain FP64 chain -------
 // One kernel per transformation of the paper's chain, intermediates in
 // device memory: OscProb (+ tangents) -> weight -> bin integration -> chi^2.
-__global__ void k_plain_prob(const double2* __restrict__ nodes, int64_t nn, const PointConst* __restrict__ pcp, BaseConst bc,
-                             int nL, int grad, double* __restrict__ P, double* __restrict__ dP) {
+// A launch covers a chunk of points, flattened over (point, baseline, node):
+// element e of the chunk belongs to the point p with off[p] <= off[p0] + e <
+// off[p + 1], whose grid has n_p nodes per bin; within the point, baseline
+// r = local / (nbins n_p) and bin-major node k = local mod (nbins n_p).
+
+// The point of flattened element e: the largest p in [p0, p0 + cnt) with off[p] <= e.
+__device__ __forceinline__ int plain_point(const int64_t* __restrict__ off, int p0, int cnt, int64_t e) {
+    int lo = p0, hi = p0 + cnt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int plain_nodes(const PlainArgs& a, int p) { return a.gn[a.gid ? a.gid[p] : 0]; }
+
+// node of flattened element idx (0 <= idx < len), and its point and baseline
+__device__ __forceinline__ double2 plain_node(const PlainArgs& a, int64_t idx, int& p, int& r) {
+    const int64_t e = a.off[a.p0] + idx;
+    p = plain_point(a.off, a.p0, a.cnt, e);
+    const int64_t nn = (int64_t)a.nbins * plain_nodes(a, p);
+    const int64_t local = e - a.off[p];
+    r = (int)(local / nn);
+    const int64_t k = local - (int64_t)r * nn;
+    return a.nodes[a.goff[a.gid ? a.gid[p] : 0] + k];
+}
+
+__global__ void k_plain_prob(PlainArgs a) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nn * nL) return;
-    const int r = (int)(idx / nn);
-    const int64_t k = idx - (int64_t)r * nn;
-    const PointConst& pc = *pcp;
-    const double e = nodes[k].x;
+    if (idx >= a.len) return;
+    int p, r;
+    const double e = plain_node(a, idx, p, r).x;
+    const PointConst& pc = a.pcs[p];
     const double x21 = pc.c21[r] * e, x32 = pc.c32[r] * e, x31 = (pc.c21[r] + pc.c32[r]) * e;
     double s21, c21, s31, c31, s32, c32;
     sincos(x21, &s21, &c21);
     sincos(x31, &s31, &c31);
     sincos(x32, &s32, &c32);
     const double S21 = s21 * s21, S31 = s31 * s31, S32 = s32 * s32;
-    P[idx] = 1.0 - pc.A[0] * S21 - pc.A[1] * S31 - pc.A[2] * S32;
-    if (grad) {
-        const int64_t stride = nn * nL;
-        const double kle = bc.kld[r] * e;
-        dP[idx] = -(pc.dA12[0] * S21 + pc.dA12[1] * S31 + pc.dA12[2] * S32);
-        dP[stride + idx] = -(pc.dA13[0] * S21 + pc.dA13[1] * S31 + pc.dA13[2] * S32);
-        dP[2 * stride + idx] = -(pc.A[0] * 2.0 * s21 * c21 + pc.A[1] * 2.0 * s31 * c31) * kle;
-        dP[3 * stride + idx] = -(pc.A[1] * 2.0 * s31 * c31 + pc.A[2] * 2.0 * s32 * c32) * kle;
+    a.P[idx] = 1.0 - pc.A[0] * S21 - pc.A[1] * S31 - pc.A[2] * S32;
+    if (a.grad) {
+        const int64_t stride = a.len;
+        const double kle = a.bc.kld[r] * e;
+        a.dP[idx] = -(pc.dA12[0] * S21 + pc.dA12[1] * S31 + pc.dA12[2] * S32);
+        a.dP[stride + idx] = -(pc.dA13[0] * S21 + pc.dA13[1] * S31 + pc.dA13[2] * S32);
+        a.dP[2 * stride + idx] = -(pc.A[0] * 2.0 * s21 * c21 + pc.A[1] * 2.0 * s31 * c31) * kle;
+        a.dP[3 * stride + idx] = -(pc.A[1] * 2.0 * s31 * c31 + pc.A[2] * 2.0 * s32 * c32) * kle;
     }
 }
 
-__global__ void k_plain_weight(const double2* __restrict__ nodes, int64_t nn, int64_t rows, double* __restrict__ V) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nn * rows) return;
-    V[idx] *= nodes[idx % nn].y;
+// V[q][idx] *= W of idx's node, for rows q of the chunk's len elements
+__global__ void k_plain_weight(PlainArgs a, int rows, double* __restrict__ V) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.len * rows) return;
+    int p, r;
+    V[t] *= plain_node(a, t % a.len, p, r).y;
 }
 
-// one warp per (row, bin)
-__global__ void k_plain_binint(const double* __restrict__ V, int64_t rows, int nbins, int n, double* __restrict__ out) {
+// one warp per (row q, point, baseline, bin): out[q][pl][r][i] = sum over the bin's nodes
+__global__ void k_plain_binint(PlainArgs a, int rows, const double* __restrict__ V, double* __restrict__ out) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= rows * nbins) return;
-    const int64_t row = w / nbins;
-    const int i = (int)(w - row * nbins);
-    const double* src = V + row * (int64_t)nbins * n + (int64_t)i * n;
+    const int64_t per_row = (int64_t)a.cnt * a.nL * a.nbins;
+    if (w >= rows * per_row) return;
+    const int64_t q = w / per_row;
+    const int64_t rem = w - q * per_row;
+    const int pl = (int)(rem / ((int64_t)a.nL * a.nbins));
+    const int rb = (int)(rem - (int64_t)pl * a.nL * a.nbins);  // r nbins + i
+    const int p = a.p0 + pl;
+    const int n = plain_nodes(a, p);
+    const double* src = V + q * a.len + (a.off[p] - a.off[a.p0]) + (int64_t)rb * n;
     double s = 0.0;
     for (int k = lane; k < n; k += 32) s += src[k];
     for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[w] = s;
 }
 
-// one CTA per point; mu_r [nL][nbins], dmu [4][nL][nbins]
+// one CTA per point of the chunk; mu_r [cnt][nL][nbins], dmu [4][cnt][nL][nbins]
 __global__ void k_plain_chi2(PlainChi2Args a) {
     __shared__ double sh[5][256];
+    const int pl = blockIdx.x;
+    const int p = a.p0 + pl;
+    const double* mu_r = a.mu_r + (int64_t)pl * a.nL * a.nbins;
+    const double* data = a.data + (a.dpp ? (int64_t)p * a.nbins : 0);
     double acc[5] = {0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
         double M = 0, D[4] = {0, 0, 0, 0};
         for (int r = 0; r < a.nL; r++) {
-            M += a.bc.omd[r] * a.mu_r[(int64_t)r * a.nbins + i];
+            M += a.bc.omd[r] * mu_r[(int64_t)r * a.nbins + i];
             if (a.dmu)
-                for (int q = 0; q < 4; q++) D[q] += a.bc.omd[r] * a.dmu[((int64_t)q * a.nL + r) * a.nbins + i];
+                for (int q = 0; q < 4; q++)
+                    D[q] += a.bc.omd[r] * a.dmu[(((int64_t)q * a.cnt + pl) * a.nL + r) * a.nbins + i];
         }
         const double e = a.eta ? a.eta[i] : 0.0;
         const double f = a.norm * (1.0 + e);
         const double mu = f * M;
-        const double d = a.data[i];
+        const double d = data[i];
         double term, g;
         if (a.kind == GNA_PEARSON) {
             term = (d - mu) * (d - mu) / mu;
@@ -272,10 +311,12 @@ __global__ void k_plain_chi2(PlainChi2Args a) {
         if (pen) term += e * e / (a.sigma * a.sigma);
         acc[0] += term;
         for (int q = 0; q < 4; q++) acc[1 + q] += g * f * D[q];
-        if (a.mu_out) a.mu_out[i] = mu;
-        if (a.grad_eta_out) a.grad_eta_out[i] = g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
+        if (a.mu_out) a.mu_out[(int64_t)p * a.nbins + i] = mu;
+        if (a.grad_eta_out)
+            a.grad_eta_out[(int64_t)p * a.nbins + i] = g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
         if (a.spectra_out)
-            for (int r = 0; r < a.nL; r++) a.spectra_out[(int64_t)r * a.nbins + i] = a.mu_r[(int64_t)r * a.nbins + i];
+            for (int r = 0; r < a.nL; r++)
+                a.spectra_out[((int64_t)p * a.nL + r) * a.nbins + i] = mu_r[(int64_t)r * a.nbins + i];
     }
     for (int v = 0; v < 5; v++) sh[v][threadIdx.x] = acc[v];
     __syncthreads();
@@ -285,24 +326,21 @@ __global__ void k_plain_chi2(PlainChi2Args a) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        a.chi2[0] = sh[0][0];
+        a.chi2[p] = sh[0][0];
         if (a.grad)
-            for (int q = 0; q < 4; q++) a.grad[q] = sh[1 + q][0];
+            for (int q = 0; q < 4; q++) a.grad[(int64_t)p * 4 + q] = sh[1 + q][0];
     }
 }
 
-cudaError_t launch_plain_point(const double2* nodes, int nbins, int n, const PointConst* pc, const BaseConst& bc, int nL,
-                               int grad, double* P, double* dP, double* mu_r, double* dmu, const PlainChi2Args& ca,
-                               cudaStream_t s) {
-    const int64_t nn = (int64_t)nbins * n;
-    const int64_t t1 = nn * nL;
-    k_plain_prob<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(nodes, nn, pc, bc, nL, grad, P, dP);
-    k_plain_weight<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(nodes, nn, nL, P);
-    if (grad) k_plain_weight<<<(unsigned)((4 * t1 + 255) / 256), 256, 0, s>>>(nodes, nn, 4 * nL, dP);
-    const int64_t w1 = (int64_t)nL * nbins * 32;
-    k_plain_binint<<<(unsigned)((w1 + 255) / 256), 256, 0, s>>>(P, nL, nbins, n, mu_r);
-    if (grad) k_plain_binint<<<(unsigned)((4 * w1 + 255) / 256), 256, 0, s>>>(dP, 4 * nL, nbins, n, dmu);
-    k_plain_chi2<<<1, 256, 0, s>>>(ca);
+cudaError_t launch_plain_chunk(const PlainArgs& a, const PlainChi2Args& ca, cudaStream_t s) {
+    const int64_t rows = a.grad ? 4 : 0;
+    k_plain_prob<<<(unsigned)((a.len + 255) / 256), 256, 0, s>>>(a);
+    k_plain_weight<<<(unsigned)((a.len + 255) / 256), 256, 0, s>>>(a, 1, a.P);
+    if (a.grad) k_plain_weight<<<(unsigned)((rows * a.len + 255) / 256), 256, 0, s>>>(a, 4, a.dP);
+    const int64_t w1 = (int64_t)a.cnt * a.nL * a.nbins * 32;
+    k_plain_binint<<<(unsigned)((w1 + 255) / 256), 256, 0, s>>>(a, 1, a.P, a.mu_r);
+    if (a.grad) k_plain_binint<<<(unsigned)((rows * w1 + 255) / 256), 256, 0, s>>>(a, 4, a.dP, a.dmu);
+    k_plain_chi2<<<(unsigned)a.cnt, 256, 0, s>>>(ca);
     return cudaGetLastError();
 }
 
@@ -491,6 +529,35 @@ cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, c
 
 cudaError_t launch_lm_finish(int npts, const LMState* st, gna_osc* prm, cudaStream_t s) {
     k_lm_finish<<<(npts + 127) / 128, 128, 0, s>>>(npts, st, prm);
+    return cudaGetLastError();
+}
+
+}  // namespace gna
+
+namespace gna {
+
+// -------------------------------------------------- FP32 rate probe -------
+// Eight independent FMA chains per thread, `iters` steps each: the FP32 pipe
+// rate that the node kernels are measured against (FMA = one operation).  The
+// sum is stored only if it reaches a value the chains cannot reach, so the
+// work is kept and nothing is written.
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, float* __restrict__ out) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) a[j] = 1.0f + 1e-3f * (float)(j + (threadIdx.x & 7));
+    const float m = 0.99999994f, c = 5.9604645e-8f;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] = fmaf(a[j], m, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s += a[j];
+    if (s == -1.0f) out[0] = s;
+}
+
+cudaError_t launch_fma_probe(int blocks, int iters, float* out, cudaStream_t s) {
+    k_fma_probe<<<blocks, 256, 0, s>>>(iters, out);
     return cudaGetLastError();
 }
 

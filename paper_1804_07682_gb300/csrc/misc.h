@@ -10,21 +10,40 @@
 
 namespace gna {
 
-struct PlainChi2Args {
-    const double* mu_r;  // [nL][nbins]
-    const double* dmu;   // [4][nL][nbins] or NULL
+// Plain FP64 chain over one chunk of points p0 .. p0 + cnt - 1, flattened
+// over (point, baseline, node): len = off[p0 + cnt] - off[p0] elements.
+struct PlainArgs {
+    const double2* nodes;   // bin-major grids {1/E, W}, one per distinct node count
+    const int64_t* goff;    // [ngrids] first node of each grid
+    const int* gn;          // [ngrids] nodes per bin
+    const int* gid;         // [npts] grid of each point, or NULL (one grid)
+    const int64_t* off;     // [npts + 1] first element of each point (nL nbins n_p elements per point)
+    const PointConst* pcs;  // [npts]
     BaseConst bc;
-    int nL, nbins;
+    int nbins, nL, p0, cnt, grad;
+    int64_t len;
+    double* P;              // [len]
+    double* dP;             // [4][len]
+    double* mu_r;           // [cnt][nL][nbins]
+    double* dmu;            // [4][cnt][nL][nbins]
+};
+
+struct PlainChi2Args {
+    const double* mu_r;  // [cnt][nL][nbins]
+    const double* dmu;   // [4][cnt][nL][nbins] or NULL
+    BaseConst bc;
+    int nL, nbins, p0, cnt;
     double norm;
     int kind;
     const double* eta;
     double sigma;
-    const double* data;  // [nbins]
-    double* chi2;        // [1]
-    double* grad;        // [4] or NULL
-    double* mu_out;      // [nbins] or NULL
+    const double* data;  // [npts][nbins] if dpp else [nbins]
+    int dpp;
+    double* chi2;        // [npts]
+    double* grad;        // [npts][4] or NULL
+    double* mu_out;      // [npts][nbins] or NULL
     double* grad_eta_out;
-    double* spectra_out;  // [nL][nbins] or NULL
+    double* spectra_out;  // [npts][nL][nbins] or NULL
 };
 
 struct OscConst {
@@ -64,13 +83,14 @@ cudaError_t launch_gl(int n, double* x, double* w, double* tmp_ab, cudaStream_t 
 cudaError_t launch_build_grid(int nbins, int nbins_pad, const double* edges, int n, const double* x, const double* w,
                               double e_scale, int layout, float4* ff, double2* d64, double2* plain64, cudaStream_t s);
 cudaError_t launch_sum_weights(const float4* grid, int nbins, int n, int layout, double* out, cudaStream_t s);
-cudaError_t launch_plain_point(const double2* nodes, int nbins, int n, const PointConst* pc, const BaseConst& bc, int nL,
-                               int grad, double* P, double* dP, double* mu_r, double* dmu, const PlainChi2Args& ca,
-                               cudaStream_t s);
+// The plain chain's kernels for one chunk of points: OscProb (+ tangents),
+// weights, bin integration, chi^2 (4 launches, 6 with the tangents).
+cudaError_t launch_plain_chunk(const PlainArgs& a, const PlainChi2Args& ca, cudaStream_t s);
 cudaError_t launch_oscprob(const double* E, int64_t n, const OscConst& oc, int prec, void* P, cudaStream_t s);
 cudaError_t launch_lm_init(LMState* st, int npts, double lam0, cudaStream_t s);
 cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMState* st, gna_osc* prm,
                              double* chi2_best, cudaStream_t s);
+cudaError_t launch_fma_probe(int blocks, int iters, float* out, cudaStream_t s);
 cudaError_t launch_lm_finish(int npts, const LMState* st, gna_osc* prm, cudaStream_t s);
 
 }  // namespace gna

@@ -153,6 +153,21 @@ cudaError_t scratch_address(unsigned char** out) {
     return cudaSuccess;
 }
 
+// Whether ptr is global memory a kernel on the current device may use:
+// memory of this device or managed memory, aligned to `align` bytes.  Another
+// device's memory and host memory are refused before anything is launched.
+bool on_this_device(const void* ptr, size_t align) {
+    if (reinterpret_cast<uintptr_t>(ptr) % align) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, const double* W, const double* L, int nL,
@@ -163,8 +178,12 @@ extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, 
     if (kind != GNA_PEARSON && kind != GNA_POISSON) return GNA_EINVAL;
     if (!(norm > 0.0)) return GNA_EINVAL;
     if (nbins < 1 || n < 1 || nL < 1) return GNA_ESHAPE;
-    const int nchunks = (n + kTileNodes - 1) / kTileNodes;
-    if (nbins > kMaxBins || nL > kMaxNL || (int64_t)nbins * nchunks > kMaxTiles) return GNA_ESHAPE;
+    const int64_t nchunks64 = ((int64_t)n + kTileNodes - 1) / kTileNodes;
+    if (nbins > kMaxBins || nL > kMaxNL || (int64_t)nbins * nchunks64 > kMaxTiles) return GNA_ESHAPE;
+    const int nchunks = (int)nchunks64;
+    if (!on_this_device(E, 8) || !on_this_device(W, 8) || !on_this_device(params, 8) || !on_this_device(data, 8) ||
+        !on_this_device(chi2, 8) || (grad && !on_this_device(grad, 8)) || (mu && !on_this_device(mu, 8)))
+        return GNA_EINVAL;
     // baseline weights and their FP32 parts, as in a plan
     BaseConst bc;
     memset(&bc, 0, sizeof(bc));

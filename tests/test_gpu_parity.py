@@ -2,10 +2,12 @@
 
 Tolerances (from the workload definition): FP64 mode 1e-9 relative on chi^2,
 mu and spectra and 1e-9 normwise on the gradient; mixed modes 1e-6 relative on
-P, mu and spectra (gradient reported with a loose 1e-4 sanity bound).  chi^2
-is compared at the same tolerance scaled by max(chi2, sum_i |g_i| mu_i): the
-largest chi^2 change a relative change of every mu_i can cause (plain
-relative error whenever chi^2 dominates).
+P, mu, spectra and chi^2 (gradient reported with a loose 1e-4 sanity bound).
+chi^2 is held to the plain relative tolerance and, in addition, to the same
+tolerance scaled by max(chi2, sum_i |g_i| mu_i) -- the largest chi^2 change a
+relative change of every mu_i can cause.  Two mixed-precision cases keep only
+the scaled bound, each with its measured reason at the test: bins of 3-16
+nodes, and one bin whose chi^2 is 338x below that scale.
 """
 import ctypes
 
@@ -17,7 +19,7 @@ torch = pytest.importorskip("torch")
 import oracle
 from paper_1804_07682_gb300 import _native as N
 from paper_1804_07682_gb300 import workloads as wl
-from refs import Case, chi2_err_bound, normrel, rel
+from refs import Case, check_chi2, log_err, normrel, rel
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
@@ -216,7 +218,7 @@ def get_case(name):
     return _case_cache[name]
 
 
-def check_chain(api, case, prec, mapping=None, spectra=True):
+def check_chain(api, case, prec, mapping=None, spectra=True, plain_chi2=True):
     w = case.w
     per_point = case.data.ndim == 2
     plan = make_plan(api, case, prec, mapping, per_point_data=per_point)
@@ -228,8 +230,8 @@ def check_chain(api, case, prec, mapping=None, spectra=True):
     tol, gtol = TOL[prec], GTOL[prec]
     for p in range(w.npts):
         ref = case.oracle_point(p)
-        scale = chi2_err_bound(ref, case.data_of(p), w.kind)
-        assert abs(out["chi2"][p].item() - ref["chi2"]) <= tol * scale, (p, out["chi2"][p].item(), ref["chi2"], scale)
+        check_chi2(out["chi2"][p].item(), ref, case.data_of(p), w.kind, tol, tag="chain %s %s %s p%d" % (
+            w.name, prec, mapping, p), plain=plain_chi2)
         assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < tol
         if spectra:
             assert rel(out["spectra"][p].cpu().numpy(), ref["mu_rb"]) < tol
@@ -262,7 +264,7 @@ def test_slice_shapes(api, prec, tuning):
     out = plan.eval(plan.params_tensor(w.theta), dev(case.data), grad=True, mu=True, spectra=True)
     ref = case.oracle_point(0)
     tol = TOL[prec]
-    assert abs(out["chi2"][0].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, case.data, w.kind)
+    check_chi2(out["chi2"][0].item(), ref, case.data, w.kind, tol, tag="slice_shapes %s %s" % (prec, tuning))
     assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < tol
     assert rel(out["spectra"][0].cpu().numpy(), ref["mu_rb"]) < tol
     assert normrel(out["grad"][0].cpu().numpy(), ref["grad"][:4]) < GTOL[prec]
@@ -321,8 +323,12 @@ def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):
     theta = np.tile(np.array(wl.TRUTH), (npts, 1)) * rng.uniform(0.9, 1.1, size=(npts, 4))
     w = wl.Workload("tiny", np.linspace(2.0, 8.0, nbins + 1), n, np.array([52.5, 53.0]), theta, wl.POISSON)
     case = Case(w)
+    # bins of 3-16 nodes: in the mixed precisions a node's P carries ~1e-7 of
+    # FP32 rounding that so few nodes cannot average, and chi^2 here is 36-54x
+    # below its error scale sum_i |g_i| mu_i (measured up to 6.8e-6 relative):
+    # the scaled bound only; GNA_FP64 keeps the plain relative 1e-9
     for prec in (("f64phase", "ff") if mapping == "slices" else ("fp64", "ff")):
-        check_chain(api, case, prec, mapping)
+        check_chain(api, case, prec, mapping, plain_chi2=(prec == "fp64"))
 
 
 @pytest.mark.parametrize("nL", [3, 5, 12, 16])
@@ -349,9 +355,11 @@ def test_many_bins(api, prec, mapping):
 @pytest.mark.parametrize("prec,mapping", [("fp64", None), ("ff", "split"), ("ff", "slices"), ("f64phase", "slices")])
 def test_one_bin_of_many_nodes(api, prec, mapping):
     # one bin (one lane of one group busy) of 16384 nodes, eight baselines:
-    # the slice mapping cuts it into its largest number of slices
+    # the slice mapping cuts it into its largest number of slices.  Its chi^2
+    # (3.5) is 338x below sum |g| mu, so the mixed precisions' 4e-9 relative
+    # error of mu shows as 1.4e-6 on chi^2 (measured): the scaled bound there
     w = wl.shrink(wl.reactor8_1000x16384(), nbins=1)
-    check_chain(api, Case(w), prec, mapping)
+    check_chain(api, Case(w), prec, mapping, plain_chi2=(prec == "fp64"))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
@@ -367,16 +375,31 @@ def test_points_sharing_grids(api, prec):
     check_chain(api, Case(w), prec)
 
 
-def test_plain_chain_matches_oracle(api):
-    case = get_case("reactor8_40x3000")
+@pytest.mark.parametrize("name", ["reactor8_40x3000", "scan_16pts_60bins", "fits_8x100x20", "nuisance_64x1000",
+                                  "reactor_200x50"])
+def test_plain_chain_matches_oracle(api, name):
+    # the plain FP64 one-kernel-per-transformation chain: eight baselines,
+    # uneven per-point grids (16 points, points sharing grids), one data row
+    # per point, nuisances; every point against the oracle at 1e-9
+    case = get_case(name)
     w = case.w
-    plan = make_plan(api, case, "ff", with_plain=True)
-    out = plan.eval(plan.params_tensor(w.theta), dev(case.data), grad=True, mu=True, spectra=True, plain=True)
-    ref = case.oracle_point(0)
-    assert rel(out["chi2"][0].item(), ref["chi2"]) < 1e-9
-    assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < 1e-9
-    assert rel(out["spectra"][0].cpu().numpy(), ref["mu_rb"]) < 1e-9
-    assert normrel(out["grad"][0].cpu().numpy(), ref["grad"][:4]) < 1e-9
+    per_point = case.data.ndim == 2
+    plan = make_plan(api, case, "ff", with_plain=True, per_point_data=per_point)
+    eta = None if w.eta is None else dev(w.eta)
+    out = plan.eval(plan.params_tensor(w.theta), dev(case.data), eta, w.sigma_eta, grad=True,
+                    grad_eta=eta is not None, mu=True, spectra=True, plain=True)
+    torch.cuda.synchronize()
+    plan.status()
+    assert plan.launches == 1 + 6  # prepare, then one chunk of six kernels
+    for p in range(w.npts):
+        ref = case.oracle_point(p)
+        check_chi2(out["chi2"][p].item(), ref, case.data_of(p), w.kind, 1e-9, tag="plain %s p%d" % (name, p))
+        assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < 1e-9
+        assert rel(out["spectra"][p].cpu().numpy(), ref["mu_rb"]) < 1e-9
+        assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:4]) < 1e-9
+        if eta is not None:
+            assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][4:]) < 1e-9
+    plan.close()
 
 
 def test_sampled_kernel_profiling(api):
@@ -473,7 +496,7 @@ def test_cached_epilogue_matches_full_evaluation(api, mapping):
     # against the oracle too, for the last pair
     ref = oracle.chain(w.edges, w.nodes_per_bin, w.L, w.theta[0], case.N, d2.cpu().numpy(), w.kind, eta=w.eta,
                        sigma=w.sigma_eta)
-    assert abs(c["chi2"][0].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, d2.cpu().numpy(), w.kind)
+    check_chi2(c["chi2"][0].item(), ref, d2.cpu().numpy(), w.kind, 1e-6, tag="cached " + mapping)
     assert rel(c["mu"][0].cpu().numpy(), ref["mu"]) < 1e-6
     # kept without a gradient: a gradient is refused, chi^2 alone is fine
     plan.eval(p, d, grad=False)
@@ -516,7 +539,7 @@ def test_mapping_is_a_tuning_choice_on_small_grids(api, prec):
         plan.tuning = f"mapping={m} block=128 nodes=4"
         assert plan.tuning.startswith(f"mapping={m}")
         out = plan.eval(p, d, grad=True, mu=True)
-        assert abs(out["chi2"][0].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, case.data, w.kind)
+        check_chi2(out["chi2"][0].item(), ref, case.data, w.kind, tol, tag="mapping_choice %s %s" % (prec, m))
         assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < tol
         res[m] = out["chi2"][0].item()
     assert rel(res["split"], res["bins"]) < 2 * tol
@@ -524,7 +547,7 @@ def test_mapping_is_a_tuning_choice_on_small_grids(api, prec):
     text = plan.autotune(p, d, reps=5)
     assert text.startswith("mapping=")
     out = plan.eval(p, d, grad=True)
-    assert abs(out["chi2"][0].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, case.data, w.kind)
+    check_chi2(out["chi2"][0].item(), ref, case.data, w.kind, tol, tag="mapping_choice autotuned " + prec)
     plan.close()
     # a plan whose mapping was forced keeps one layout only
     forced = make_plan(api, case, prec, "split")
@@ -675,19 +698,17 @@ def check_general(api, channel, prec, edges, counts, L, npts, e_scale, kind, see
                             0.02 if nuisances else 0.0, grad=True, grad_eta=nuisances, mu=True)
     torch.cuda.synchronize()
     plan.status()
-    # mixed precisions: the FP32 rounding of sin^2 bounds the error of a
-    # node's P absolutely (~1e-7), so mu is held to 1e-6 relative plus 1e-7 of
-    # the bin's count at P = 1 (a disappearance dip turns the absolute bound
-    # into a larger relative one); GNA_FP64: 1e-9 relative, gradient 1e-9
-    tol, floor, gtol = (1e-9, 1e-13, 1e-9) if prec == "fp64" else (1e-6, 1e-7, 1e-4)
-    L1 = np.atleast_1d(L)
+    # 1e-6 relative on mu in the mixed precisions, also in the bins of a
+    # disappearance dip (P ~ 0.01 there; the node pass's cosine sums keep the
+    # error relative to P); GNA_FP64: 1e-9 relative, gradient 1e-9
+    tol, gtol = (1e-9, 1e-9) if prec == "fp64" else (1e-6, 1e-4)
+    tag = "general %s%s%s %s" % (channel[0], channel[1], "bar" if channel[2] else "", prec)
     for p in range(npts):
         ref = refs[p]
-        flat = oracle.baseline_weights(L1) @ oracle.binned(edges, int(counts[p]), L1, (0.3, 0.02, 0.0, 0.0), e_scale)
-        scale = N * (1.0 + (0.0 if eta is None else eta)) * flat
-        assert abs(out["chi2"][p].item() - ref["chi2"]) <= tol * chi2_err_bound(ref, data, kind), p
-        err = np.abs(out["mu"][p].cpu().numpy() - ref["mu"])
-        assert np.all(err <= tol * np.abs(ref["mu"]) + floor * scale), (p, float((err / ref["mu"]).max()))
+        check_chi2(out["chi2"][p].item(), ref, data, kind, tol, tag="%s p%d" % (tag, p))
+        mu_err = rel(out["mu"][p].cpu().numpy(), ref["mu"])
+        log_err(tag + " mu", mu_rel=mu_err, p_min=float(np.min(ref["mu"] / np.max(ref["mu"]))))
+        assert mu_err < tol, (p, mu_err)
         assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:6]) < gtol, p
         if nuisances:
             assert normrel(out["grad_eta"][p].cpu().numpy(), ref["grad"][6:]) < gtol, p
@@ -704,6 +725,16 @@ def test_general_chain_long_baseline(api, channel, prec):
     # 810 km, 0.5-5 GeV (energies in MeV, spectrum in GeV), 3 points on one
     # grid of 40 bins x 24 nodes: the slice mapping
     check_general(api, channel, prec, np.linspace(500.0, 5000.0, 41), 24, np.array([810.0]), 3, 1e-3, 1, 7)
+
+
+@pytest.mark.parametrize("L", [[810.0], [810.0, 790.0, 830.0]])
+@pytest.mark.parametrize("channel", [("mu", "mu", False), ("mu", "mu", True), ("tau", "tau", False)])
+@pytest.mark.parametrize("prec", ["ff", "f64phase", "fp64"])
+def test_general_chain_disappearance_dip(api, channel, prec, L):
+    # 60 narrow bins of 8 nodes around the first disappearance maximum at
+    # 810 km (1.2-2.2 GeV, P down to ~0.01): every bin's mu within 1e-6 of
+    # the oracle with no absolute allowance, one and three baselines
+    check_general(api, channel, prec, np.linspace(1200.0, 2200.0, 61), 8, np.array(L), 2, 1e-3, 1, 17)
 
 
 @pytest.mark.parametrize("channel", [("mu", "e", False), ("e", "e", True)])
@@ -768,7 +799,7 @@ def test_general_chain_per_point_data_and_chi2_only(api, prec):
     assert "grad" not in out
     for p in range(3):
         ref = oracle.chain_general(edges, 40, [810.0], theta[p], N, rows[p], "mu", "e", False, 1, e_scale=1e-3)
-        assert abs(out["chi2"][p].item() - ref["chi2"]) <= 1e-6 * chi2_err_bound(ref, rows[p], 1), p
+        check_chi2(out["chi2"][p].item(), ref, rows[p], 1, TOL[prec], tag="general rows %s p%d" % (prec, p))
         assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < 1e-6, p
     plan.close()
 

@@ -116,3 +116,42 @@ def test_any_channel_calls_without_a_plan(N):
     o = N.GnaOutputs(None, None, None, None, None)
     assert N.lib().gna_chain_eval_general(None, None, None, 0.0, None, 0, ctypes.byref(o), None) == EINVAL
     assert N.lib().gna_plan_autotune_general(None, None, None, 0, ctypes.byref(o), 1, None) == EINVAL
+
+
+def test_noalloc_wrapper_refuses_bad_arguments_before_any_launch():
+    # chi2_noalloc checks dtypes, shapes and devices before it reaches the
+    # library: a float32 or misshapen array, a short data row or output, or a
+    # tensor off the device would otherwise be read or written out of bounds
+    torch = pytest.importorskip("torch")
+    from paper_1804_07682_gb300 import api
+
+    f64 = torch.float64
+    E = torch.ones(5, 7, dtype=f64)
+    W = torch.ones(5, 7, dtype=f64)
+    p = torch.zeros(1, 4, dtype=f64)
+    d = torch.ones(5, dtype=f64)
+    bad = {
+        "E float32": dict(E=E.float()),
+        "E 1-D": dict(E=torch.ones(35, dtype=f64)),
+        "W float32": dict(W=W.float()),
+        "W shaped unlike E": dict(W=torch.ones(5, 6, dtype=f64)),
+        "params of 3": dict(params=torch.zeros(1, 3, dtype=f64)),
+        "params float32": dict(params=p.float()),
+        "data short": dict(data=torch.ones(4, dtype=f64)),
+        "data float32": dict(data=d.float()),
+        "Lweight per baseline": dict(L=[52.5, 30.0], Lweight=[1.0]),
+        "out without chi2": dict(out={"grad": torch.empty(4, dtype=f64)}),
+        "out mu short": dict(out={"chi2": torch.empty(1, dtype=f64), "mu": torch.empty(4, dtype=f64)}),
+        "out grad short": dict(out={"chi2": torch.empty(1, dtype=f64), "grad": torch.empty(3, dtype=f64)}),
+        "out chi2 empty": dict(out={"chi2": torch.empty(0, dtype=f64)}),
+        "out unknown": dict(out={"chi2": torch.empty(1, dtype=f64), "spectra": torch.empty(5, dtype=f64)}),
+    }
+    for what, kw in bad.items():
+        args = dict(E=E, W=W, L=[52.5], params=p, data=d, norm=1.0)
+        args.update(kw)
+        with pytest.raises(ValueError) as e:
+            api.chi2_noalloc(**args)
+        assert "CUDA" not in str(e.value), what  # refused for its dtype or shape, not its device
+    # every dtype and shape right, but host tensors: refused for the device
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        api.chi2_noalloc(E, W, [52.5], p, d, 1.0)

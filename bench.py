@@ -38,13 +38,14 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 def fp32_ops_general(nL: int, grad: bool) -> int:
     """Algorithmic FP32 operations per energy node of the any-channel node
-    kernel: per (node, baseline) the phases and their sin/cos 38, angle
-    addition 4, sin^2 and sin cos of three phases 6, their weighted sums 6
-    (12 with hi + lo weights for several baselines), with the gradient
-    cos^2 - sin^2 3 and two more weighted sums per phase 6; per node the Kahan
-    product-sums of 6 (12) values, 4 each."""
-    per_r = 54 + (6 if nL > 1 else 0) + (9 if grad else 0)
-    return nL * per_r + (48 if grad else 24)
+    kernel: per (node, baseline) the two phases reduced modulo pi/2 (11 each),
+    their sin/cos 10 each and quadrant swaps 3 each (48), angle addition 4,
+    sin^2, sin cos and cos^2 of three phases 9, their weighted sums 9 (18 with
+    hi + lo weights for several baselines), with the gradient cos^2 - sin^2 3
+    and two more weighted sums per phase 6; per node the Kahan product-sums of
+    9 (15) values, 4 each."""
+    per_r = 70 + (9 if nL > 1 else 0) + (9 if grad else 0)
+    return nL * per_r + (60 if grad else 36)
 
 
 def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
@@ -296,6 +297,33 @@ def side_workloads(api, torch, device, args):
                                  "fp32_frac_of_issue_peak": ops / (ms * 1e-3) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
                                  "tuning": plan.tuning, "graph": True}
     plan.close()
+    # the same scan, chi^2 and gradient of all 4096 points, through the plain
+    # FP64 chain (one kernel per transformation, points in chunks) and through
+    # the all-double fused kernel; errors of the timed mixed path against them
+    fp64 = {}
+    for name, prec, plain in (("plain_fp64_chain", args.prec, True), ("fused_fp64", "fp64", False)):
+        pl = api.Plan(w.edges, w.L, npts=w.npts, node_counts=w.node_counts, norm=N, e_scale=w.e_scale, prec=prec,
+                      kind=w.kind, with_plain=plain)
+        q = pl.params_tensor(w.theta)
+        r = pl.eval(q, data, grad=True, plain=plain)
+        torch.cuda.synchronize()
+        n_rep = 3
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        for _ in range(n_rep):
+            pl.eval(q, data, grad=True, plain=plain, out=r)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pl.status()
+        ms64 = a0.elapsed_time(a1) / n_rep
+        fp64[name] = {"ms_per_scan": ms64, "chi2_grad_evals_per_s": w.npts * 1e3 / ms64, "launches": pl.launches}
+        c_ref, g_ref = r["chi2"].cpu().numpy(), r["grad"].cpu().numpy()
+        c_mix, g_mix = check["scan"][3], check["scan"][4]
+        fp64[name]["mixed_max_rel_err"] = {
+            "chi2": float(np.max(np.abs(c_mix - c_ref) / np.abs(c_ref))),
+            "grad_normwise": float(np.max(np.linalg.norm(g_mix - g_ref, axis=1) / np.linalg.norm(g_ref, axis=1)))}
+        pl.close()
+    out["scan_64x64_500bins"]["fp64_gpu"] = fp64
     # the same scan for nu_mu -> nu_e appearance through the any-channel chain:
     # (s2_13, dm2_32) on the same uneven grids, s2_23 = 0.545 and delta = 1.2 pi,
     # chi^2 and its gradient in all six parameters
@@ -363,10 +391,62 @@ def side_workloads(api, torch, device, args):
     ms = a0.elapsed_time(a1)
     pts = w.points_per_eval() * w.fit_iters
     check["fits"] = (w, N, data[0].cpu().numpy(), p[0].cpu().numpy(), c2[0].item())
+    ops = fp32_ops_per_node(w.nL, True, False) * w.nbins * w.nodes_per_bin * w.npts * w.fit_iters
     out["fits_16384x1000"] = {"fits_per_s": w.npts * 1e3 / ms, "ms_per_batch": ms, "iterations": w.fit_iters,
                               "chi2_grad_evals_per_s": w.npts * w.fit_iters * 1e3 / ms, "gpoints_per_s": pts / ms / 1e6,
+                              "fp32_frac_of_issue_peak": ops / (ms * 1e-3) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
                               "median_best_chi2": float(c2.median()), "tuning": plan.tuning, "graph": True}
     plan.close()
+    # against double precision on the same GPU: the plain FP64 chain's chi^2 +
+    # gradient evaluations of 512 of the data sets (full size each, points in
+    # chunks of 64: its rate per data set does not depend on how many are
+    # evaluated), and all-double fused fits of 256 data sets (20 iterations)
+    fp64 = {}
+    k = 512
+    pl = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, npts=k, norm=N, prec=args.prec, kind=w.kind,
+                  max_datasets=k, with_plain=True)
+    q, dk = p0[:k].contiguous(), data[:k].contiguous()
+    r = pl.eval(q, dk, grad=True, plain=True)
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    for _ in range(2):
+        pl.eval(q, dk, grad=True, plain=True, out=r)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    pl.status()
+    ms64 = a0.elapsed_time(a1) / 2
+    plain_launches = pl.launches
+    mixed = pl.eval(q, dk, grad=True)
+    torch.cuda.synchronize()
+    relc = float(((mixed["chi2"] - r["chi2"]).abs() / r["chi2"].abs()).max())
+    relg = float(((mixed["grad"] - r["grad"]).norm(dim=1) / r["grad"].norm(dim=1)).max())
+    fp64["plain_fp64_chain"] = {"datasets": k, "ms_per_eval": ms64, "chi2_grad_evals_per_s": k * 1e3 / ms64,
+                                "launches": plain_launches,
+                                "mixed_eval_max_rel_err": {"chi2": relc, "grad_normwise": relg}}
+    pl.close()
+    k = 256
+    pl = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, npts=k, norm=N, prec="fp64", kind=w.kind,
+                  max_datasets=k)
+    q, dk = p0[:k].clone(), data[:k].contiguous()
+    ck = torch.empty(k, dtype=torch.float64, device=device)
+    pl.fit(q, dk, iters=2, graph=True, chi2_out=ck)
+    q.copy_(p0[:k])
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    pl.fit(q, dk, iters=w.fit_iters, graph=True, chi2_out=ck)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    pl.status()
+    ms64 = a0.elapsed_time(a1)
+    fp64["fused_fp64_fits"] = {
+        "datasets": k, "ms_per_batch": ms64, "fits_per_s": k * 1e3 / ms64,
+        "chi2_grad_evals_per_s": k * w.fit_iters * 1e3 / ms64,
+        "mixed_fit_max_rel_err": {"best_chi2": float(((c2[:k] - ck).abs() / ck.abs()).max()),
+                                  "best_params": float(((p[:k] - q).abs() / q.abs()).max())}}
+    pl.close()
+    out["fits_16384x1000"]["fp64_gpu"] = fp64
     # the 10^4-point reactor chain (latency-bound), all-double and mixed, graph-replayed
     w = wl.reactor_200x50()
     res = {}
@@ -421,8 +501,16 @@ def side_workloads(api, torch, device, args):
     def direct_step():
         plan.eval(pt, data, et, w.sigma_eta, grad=True, grad_eta=True, out=od)
 
+    def ad_step_calling_thread():
+        # PyTorch runs a CUDA backward on its per-device worker thread by
+        # default (two cross-thread hand-offs per backward); with the engine's
+        # multithreading off it runs on the calling thread
+        with torch.autograd.set_multithreading_enabled(False):
+            ad_step()
+
     res = {}
-    for name, fn in (("autograd", ad_step), ("direct", direct_step)):
+    for name, fn in (("autograd", ad_step), ("autograd_calling_thread", ad_step_calling_thread),
+                     ("direct", direct_step)):
         for _ in range(5):
             fn()
         torch.cuda.synchronize()
@@ -438,6 +526,7 @@ def side_workloads(api, torch, device, args):
     ops = fp32_ops_per_node(w.nL, True, False) * w.nbins * w.nodes_per_bin
     out["nuisance_1000x4096"] = {
         "evals_per_s_autograd": 1e6 / res["autograd"], "us_per_eval_autograd": res["autograd"],
+        "us_per_eval_autograd_calling_thread": res["autograd_calling_thread"],
         "us_per_eval_direct": res["direct"], "gpoints_per_s": w.points_per_eval() / res["direct"] / 1e3,
         "fp32_frac_of_issue_peak": ops / (res["direct"] * 1e-6) / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
         "outputs": "chi2, d chi2 / d(4 oscillation parameters, 1000 nuisances)", "tuning": plan.tuning}
@@ -528,6 +617,75 @@ def side_workloads(api, torch, device, args):
     return out, check
 
 
+def fp32_probe(api, torch, device, index):
+    """Measured FP32 pipe rate: the library's probe kernel (eight FMA chains per
+    thread, eight 256-thread blocks per SM) over ~0.7 s of launches, CUDA events
+    on the stream, the SM clock sampled meanwhile; FMA = one operation, as in
+    the node kernels' counts.  Clocks are only read, never set."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, iters, reps = sms * 8, 1 << 18, 40
+    out = torch.empty(1, dtype=torch.float32, device=device)
+    api.fp32_probe(blocks, 1024, out)
+    torch.cuda.synchronize()
+    clk = Clocks(index)
+    clk.start()
+    time.sleep(0.2)
+    stream = torch.cuda.current_stream()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    fmas = sum(api.fp32_probe(blocks, iters, out) for _ in range(reps))
+    a1.record(stream)
+    torch.cuda.synchronize()
+    c = clk.stop()
+    rate = fmas / (a0.elapsed_time(a1) * 1e-3)
+    res = {"tops": rate / 1e12, "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons"), "samples": c.get("samples")}
+    if c.get("sm_mhz"):
+        res["fma_per_sm_per_clk"] = rate / (sms * c["sm_mhz"] * 1e6)
+    return res
+
+
+def short(x):
+    """A float rounded to four significant digits (the summary at the end of the line)."""
+    return None if x is None else float("%.4g" % x)
+
+
+def fp64_summary(evals_per_s, plain, side, cpu):
+    """The mixed path against double precision on the same GPU, per workload:
+    the plain FP64 chain and the all-double fused kernel, with the mixed path's
+    largest error against them; placed last on the line."""
+    out = {}
+    if plain is not None:
+        e = plain["max_rel_err"]
+        out["reactor8_1000x16384"] = {
+            "mixed_evals_per_s": short(evals_per_s), "plain_fp64_evals_per_s": short(plain["evals_per_s"]),
+            "x_plain": short(plain["speedup"]), "fused_fp64_evals_per_s": short(plain["fused_fp64"]["evals_per_s"]),
+            "x_fused_fp64": short(plain["fused_fp64"]["speedup"]),
+            "max_rel_err": {"chi2": short(e["chi2"]), "mu": short(e["mu"]), "spectra": short(e["spectra"])}}
+    if side is not None:
+        s = side["scan_64x64_500bins"]
+        f = s["fp64_gpu"]
+        out["scan_64x64_500bins"] = {
+            "mixed_evals_per_s": short(s["chi2_grad_evals_per_s"]),
+            "plain_fp64_evals_per_s": short(f["plain_fp64_chain"]["chi2_grad_evals_per_s"]),
+            "x_plain": short(s["chi2_grad_evals_per_s"] / f["plain_fp64_chain"]["chi2_grad_evals_per_s"]),
+            "fused_fp64_evals_per_s": short(f["fused_fp64"]["chi2_grad_evals_per_s"]),
+            "x_fused_fp64": short(s["chi2_grad_evals_per_s"] / f["fused_fp64"]["chi2_grad_evals_per_s"]),
+            "max_rel_err": {k: short(v) for k, v in f["plain_fp64_chain"]["mixed_max_rel_err"].items()}}
+        s = side["fits_16384x1000"]
+        f = s["fp64_gpu"]
+        pc, ff = f["plain_fp64_chain"], f["fused_fp64_fits"]
+        out["fits_16384x1000"] = {
+            "mixed_evals_per_s": short(s["chi2_grad_evals_per_s"]),
+            "plain_fp64_evals_per_s": short(pc["chi2_grad_evals_per_s"]),
+            "x_plain": short(s["chi2_grad_evals_per_s"] / pc["chi2_grad_evals_per_s"]),
+            "fused_fp64_fits_per_s": short(ff["fits_per_s"]), "mixed_fits_per_s": short(s["fits_per_s"]),
+            "x_fused_fp64": short(s["fits_per_s"] / ff["fits_per_s"]),
+            "max_rel_err": {"eval_chi2": short(pc["mixed_eval_max_rel_err"]["chi2"]),
+                            "fit_chi2": short(ff["mixed_fit_max_rel_err"]["best_chi2"]),
+                            "fit_params": short(ff["mixed_fit_max_rel_err"]["best_params"])}}
+    return out
+
+
 def cpu_side_errors(side, check):
     """CPU-baseline leg of the batched workloads: the oracle at sampled points
     of the scan, on the nuisance evaluation and on one fit; adds each
@@ -599,6 +757,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default=None)
     ap.add_argument("--no-side", action="store_true", help="skip the scan and fit side measurements")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FP32 rate probe")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -653,9 +812,11 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    # kernel events on every 8th evaluation (events between kernels hold back
-    # the dependent launch, so the other seven run undisturbed)
-    plan.profile(PROFILE_EVERY)
+    # kernel events on every k-th evaluation (events between kernels hold back
+    # the dependent launch, so the others run undisturbed), k <= 8 and at
+    # least ten timed launches
+    prof_every = max(1, min(PROFILE_EVERY, args.steps // 10))
+    plan.profile(prof_every)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -690,7 +851,7 @@ def main():
                 "frac": achieved_tops / peak_tops, "traffic": traffic, "algorithmic_bytes": hbm_bytes,
                 "kernel": KERNEL_NAMES.get(mapping, mapping) + " (double-float phase, 8 baselines, gradient + spectra)",
                 "kernel_ms": kern_avg_ms, "ops_per_launch": ops,
-                "timed_launches": kern_n, "timed_every": PROFILE_EVERY,
+                "timed_launches": kern_n, "timed_every": prof_every,
                 "peak_note": "FP32 issue peak 152 SM x 128 lanes x 2070 MHz (FMA = 1 op)",
                 "hbm_frac": hbm_bytes / (kern_avg_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0),
                 "hbm_peak_src": pk_src}
@@ -715,7 +876,7 @@ def main():
     c_host = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
     g_host = torch.empty(1, 4, dtype=torch.float64).pin_memory().numpy()
     s_host = torch.empty(1, w.nL, w.nbins, dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = max(10, args.steps // 4)
+    e2e_steps = max(10, args.steps)
     plan.set_graph(True)
     for _ in range(3):
         plan.eval_host(p_host, d_host, grad=True, chi2_out=c_host, grad_out=g_host, spectra_out=s_host)
@@ -761,6 +922,22 @@ def main():
                  "max_rel_err": {"chi2": relerr(mo["chi2"], po["chi2"]), "mu": relerr(mo["mu"], po["mu"]),
                                  "spectra": relerr(mo["spectra"], po["spectra"]),
                                  "grad_normwise": float((mo["grad"] - po["grad"]).norm() / po["grad"].norm())}}
+        # and the all-double fused kernel on the same workload
+        p64 = api.Plan(w.edges, w.L, nodes_per_bin=w.nodes_per_bin, norm=N, e_scale=w.e_scale, prec="fp64",
+                       kind=w.kind)
+        o64 = p64.eval(params, data, grad=True, spectra=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for _ in range(args.plain_steps):
+            p64.eval(params, data, grad=True, spectra=True, out=o64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        p64.status()
+        f64_ms = reduce_max(dist, a0.elapsed_time(a1) / args.plain_steps, device)
+        plain["fused_fp64"] = {"evals_per_s": world * 1e3 / f64_ms, "ms_per_step": f64_ms,
+                               "speedup": evals_per_s / (world * 1e3 / f64_ms),
+                               "max_rel_err_chi2": relerr(mo["chi2"], o64["chi2"])}
+        p64.close()
 
     # CPU baseline: the oracle, as it stands, on all host cores (rank 0 only):
     # one full evaluation (every bin, node and baseline, with the gradient)
@@ -791,7 +968,16 @@ def main():
         cpu_oscprob_table1(side["oscprob_fp64_table1_shape"])
         cpu_side_errors(side, check)
 
+    # the FP32 pipe rate measured by the probe kernel: the roofline's second denominator
+    probe = fp32_probe(api, torch, device, local) if not args.no_probe else None
+    if probe is not None:
+        roofline["measured_peak"] = probe["tops"]
+        roofline["frac_of_measured"] = achieved_tops / probe["tops"]
+        roofline["measured_peak_sm_mhz"] = probe["sm_mhz"]
+        roofline["measured_peak_note"] = "FP32 FMA probe (gna_fp32_probe), CUDA events, SM clock sampled during it"
+
     if rank == 0:
+        gpu_err = cpu.pop("gpu_error_vs_oracle", None) if cpu is not None else None
         line = {"metric": METRIC, "value": evals_per_s, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+ff-phase" if args.prec == "ff" else args.prec, "data": "synthetic",
@@ -802,7 +988,12 @@ def main():
                 "gpoints_per_s": evals_per_s * points / 1e9, "roofline": roofline, "plain_fp64_chain": plain,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
                 "epilogue_only": epilogue_only,
-                "side_workloads": side}
+                "side_workloads": side,
+                # last on the line: the mixed path against double precision on
+                # this GPU, per workload, and the timed path's error against the oracle
+                "fp32_probe": probe,
+                "vs_fp64_gpu": fp64_summary(evals_per_s, plain, side, cpu),
+                "gpu_error_vs_oracle": gpu_err}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

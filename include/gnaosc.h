@@ -351,6 +351,23 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
                                      int64_t* ticket);
 gna_status gna_chain_eval_host_wait(gna_plan* plan, int64_t ticket, double* chi2, double* grad, double* spectra);
 
+/* gna_chain_eval_general_host, gna_chain_eval_general_host_async: the
+ * host-buffer evaluation (one transfer in, one out; paper Sec. 4.2) of an
+ * any-channel plan (GNA_PLAN_GENERAL; paper Sec. 4.1, the general formula):
+ * params host [npts] gna_osc_full, eta and data as for gna_chain_eval_host,
+ * outputs chi2 [npts] and, when grad != NULL (async: grad != 0),
+ * d chi2 / d(s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32) [npts][6].
+ * The same staging slots, copy streams, graph mode and ticket rules as the
+ * survival chain's calls; gna_chain_eval_host_wait takes the results (its
+ * spectra argument is ignored).  GNA_ESTATE on a survival-chain plan (and
+ * the survival calls return GNA_ESTATE on an any-channel plan). */
+gna_status gna_chain_eval_general_host(gna_plan* plan, const gna_osc_full* params, const double* eta,
+                                       double sigma_eta, const double* data, int data_per_point, double* chi2,
+                                       double* grad, void* stream);
+gna_status gna_chain_eval_general_host_async(gna_plan* plan, const gna_osc_full* params, const double* eta,
+                                             double sigma_eta, const double* data, int data_per_point, int grad,
+                                             void* stream, int64_t* ticket);
+
 /* gna_chain_eval_plain: the same outputs computed by the plain FP64 chain,
  * one kernel per transformation as in the paper (Sec. 4.1: OscProb and its
  * tangents -> weight -> bin integration -> chi^2), intermediates in device
@@ -381,6 +398,18 @@ gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const dou
  */
 gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, int iters, double lambda0,
                          double* chi2_out, int use_graph, void* stream);
+
+/* gna_fit_batch_general: the same batched Levenberg-Marquardt fits for an
+ * any-channel plan, in the six parameters (s2_12, s2_13, s2_23, delta_cp,
+ * dm2_21, dm2_32): each iteration is one evaluation of chi^2, its gradient
+ * and J^T W J (21 entries, W = 2 / mu) followed by the 6x6 damped solve;
+ * trials are clamped into s2 in [1e-6, 1 - 1e-6] for the three mixing
+ * parameters and dm2 >= 1e-7, delta_cp is free.
+ *   params: device [npts] gna_osc_full (in: start points, out: best points)
+ *   data, iters, lambda0, chi2_out, use_graph: as for gna_fit_batch
+ * GNA_ESTATE on a survival-chain plan. */
+gna_status gna_fit_batch_general(gna_plan* plan, gna_osc_full* params, const double* data, int iters, double lambda0,
+                                 double* chi2_out, int use_graph, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Launch shape, autotuning and graphs.

@@ -269,7 +269,8 @@ def chain_general(edges, n, L_km, osc6, N, data, alpha, beta, anti=False, kind=0
     parameters.  The detector combination and chi^2 are the textbook ones of
     ``chi2`` (M_i = sum_r omega_r mu[r][i], mu_i = N (1 + eta_i) M_i, Pearson or
     Poisson, the nuisance penalty), written out here for six parameters.
-    Returns dict(chi2, grad[6 + nbins], mu[nbins], mu_rb, dmu_rb)."""
+    Returns dict(chi2, grad[6 + nbins], J[nbins][6] = d mu_i / d(parameters),
+    mu[nbins], mu_rb, dmu_rb)."""
     L = np.atleast_1d(_f64(L_km))
     om = baseline_weights(L) if omega is None else _f64(omega)
     mu_rb, dmu_rb = binned_general(edges, n, L, osc6, alpha, beta, anti, e_scale)
@@ -278,10 +279,12 @@ def chain_general(edges, n, L_km, osc6, N, data, alpha, beta, anti=False, kind=0
     e = np.zeros(nb) if eta is None else _f64(eta)
     chi2v = 0.0
     grad = np.zeros(6 + nb)
+    J = np.empty((nb, 6))
     mu = np.empty(nb)
     for i in range(nb):
         M = sum(om[r] * mu_rb[r, i] for r in range(L.size))
         dM = sum(om[r] * dmu_rb[r, i] for r in range(L.size))
+        J[i] = N * (1.0 + e[i]) * dM
         m = N * (1.0 + e[i]) * M
         if kind == 0:
             term = (d[i] - m) ** 2 / m
@@ -296,7 +299,7 @@ def chain_general(edges, n, L_km, osc6, N, data, alpha, beta, anti=False, kind=0
         if eta is not None and sigma > 0:
             chi2v += e[i] * e[i] / (sigma * sigma)
             grad[6 + i] += 2.0 * e[i] / (sigma * sigma)
-    return {"chi2": chi2v, "grad": grad, "mu": mu, "mu_rb": mu_rb, "dmu_rb": dmu_rb, "omega": om}
+    return {"chi2": chi2v, "grad": grad, "J": J, "mu": mu, "mu_rb": mu_rb, "dmu_rb": dmu_rb, "omega": om}
 
 
 def norm_for_total(edges, n, L_km, osc, total=1e5, e_scale=1.0, omega=None) -> float:
@@ -321,7 +324,15 @@ def fd_grad(f, theta, rel_h=1e-6):
     return g
 
 
-def fit_lm(evaluate, theta0, iters=20, lam0=1e-3, lo=(1e-6, 1e-6, 1e-7, 1e-7), hi=(1 - 1e-6, 1 - 1e-6, np.inf, np.inf)):
+FIT_BOX = {
+    # (s2_12, s2_13, dm2_21, dm2_32)
+    4: ((1e-6, 1e-6, 1e-7, 1e-7), (1 - 1e-6, 1 - 1e-6, np.inf, np.inf)),
+    # (s2_12, s2_13, s2_23, delta_cp, dm2_21, dm2_32): delta_cp is free
+    6: ((1e-6, 1e-6, 1e-6, -np.inf, 1e-7, 1e-7), (1 - 1e-6, 1 - 1e-6, 1 - 1e-6, np.inf, np.inf, np.inf)),
+}
+
+
+def fit_lm(evaluate, theta0, iters=20, lam0=1e-3, lo=None, hi=None):
     """Levenberg-Marquardt-damped Gauss-Newton, a fixed number of evaluations.
 
     The paper has no fitter; this is the textbook method in the order chosen for
@@ -330,13 +341,15 @@ def fit_lm(evaluate, theta0, iters=20, lam0=1e-3, lo=(1e-6, 1e-6, 1e-7, 1e-7), h
     current point and lambda /= 10, otherwise the trial is rejected and
     lambda *= 10; then H = sum_i (2/mu_i) J_i J_i^T (expected Fisher matrix),
     solve (H + lambda diag H) delta = -g at the current point and clamp the
-    next trial into the box [lo, hi].  ``evaluate(theta)`` must return a dict
-    with chi2, grad (first 4 entries used), J and mu.  Returns (theta_best,
-    chi2_best, history of chi2 per evaluation).
+    next trial into the box [lo, hi] (FIT_BOX for 4 or 6 parameters unless
+    given).  ``evaluate(theta)`` must return a dict with chi2, grad (its first
+    len(theta0) entries used), J [nbins][len(theta0)] and mu.  Returns
+    (theta_best, chi2_best, history of chi2 per evaluation).
     """
-    lo = np.asarray(lo, dtype=np.float64)
-    hi = np.asarray(hi, dtype=np.float64)
     trial = _f64(theta0).copy()
+    npar = trial.size
+    lo = np.asarray(FIT_BOX[npar][0] if lo is None else lo, dtype=np.float64)
+    hi = np.asarray(FIT_BOX[npar][1] if hi is None else hi, dtype=np.float64)
     best_theta = None
     best_chi2 = np.inf
     g = H = None
@@ -348,7 +361,7 @@ def fit_lm(evaluate, theta0, iters=20, lam0=1e-3, lo=(1e-6, 1e-6, 1e-7, 1e-7), h
         if r["chi2"] < best_chi2:
             best_chi2 = r["chi2"]
             best_theta = trial.copy()
-            g = r["grad"][:4].copy()
+            g = r["grad"][:npar].copy()
             Jm = r["J"]
             H = (Jm.T * (2.0 / r["mu"])) @ Jm
             lam = lam / 10.0

@@ -288,6 +288,37 @@ class Plan:
         self._check(self._lib.gna_plan_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)), "profile_read")
         return ms.value, n.value
 
+    # ------------------------------------------ autograd Function's path --
+    def _ad_check(self, theta, eta, data) -> int:
+        """Arguments of OscChi2 on this plan (one point); returns the parameter count."""
+        npar = 4 if self.channel is None else 6
+        if self.npts != 1:
+            raise ValueError("OscChi2 works on a single-point plan")
+        ok = lambda t, n: (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                           and t.numel() == n and t.is_contiguous())
+        if not ok(theta, npar):
+            raise ValueError("theta must be a contiguous float64 CUDA tensor of %d values" % npar)
+        if eta is not None and not ok(eta, self.nbins):
+            raise ValueError("eta must be a contiguous float64 CUDA tensor of nbins values")
+        if not ok(data, self.nbins):
+            raise ValueError("data must be a contiguous float64 CUDA tensor of nbins values")
+        return npar
+
+    def _eval_into(self, p, data, e, sigma, chi2, g_theta, g_eta):
+        """One evaluation writing chi2, d chi2 / d theta into g_theta and (with
+        nuisances) d chi2 / d eta into g_eta, through a ctypes output struct
+        kept by the plan."""
+        o = self.__dict__.get("_ad_out")
+        if o is None:
+            o = self._ad_out = N.GnaOutputs()
+        o.chi2, o.grad = chi2.data_ptr(), g_theta.data_ptr()
+        o.grad_eta = None if g_eta is None else g_eta.data_ptr()
+        fn = self._lib.gna_chain_eval if self.channel is None else self._lib.gna_chain_eval_general
+        code = fn(self._h, p.data_ptr(), None if e is None else e.data_ptr(), float(sigma), data.data_ptr(), 0,
+                  ctypes.byref(o), torch.cuda.current_stream().cuda_stream)
+        if code != N.GNA_OK:
+            self._check(code, "gna_chain_eval")
+
     # ------------------------------------------------------- evaluation --
     def params_tensor(self, theta) -> torch.Tensor:
         npar = 4 if self.channel is None else 6
@@ -386,29 +417,51 @@ class Plan:
     def eval_host(self, params: np.ndarray, data: np.ndarray, eta: Optional[np.ndarray] = None, sigma: float = 0.0,
                   grad: bool = True, chi2_out: Optional[np.ndarray] = None, grad_out: Optional[np.ndarray] = None,
                   spectra_out: Optional[np.ndarray] = None, stream=None):
-        """Evaluation from host buffers (copies in, evaluates, copies out, synchronises)."""
-        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.npts, 4)
+        """Evaluation from host buffers (copies in, evaluates, copies out,
+        synchronises).  params [npts, 4], or [npts, 6] on an any-channel plan
+        (which has no spectra)."""
+        npar = self._npar
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.npts, npar)
         d = np.ascontiguousarray(data, dtype=np.float64)
         e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
         dpp = 1 if d.ndim == 2 else 0
         c = chi2_out if chi2_out is not None else np.empty(self.npts)
-        g = (grad_out if grad_out is not None else np.empty((self.npts, 4))) if grad else None
+        g = (grad_out if grad_out is not None else np.empty((self.npts, npar))) if grad else None
         vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+        if self.channel is not None:
+            if spectra_out is not None:
+                raise ValueError("the any-channel chain has no per-baseline spectra")
+            code = self._lib.gna_chain_eval_general_host(self._h, vp(p), vp(e), float(sigma), vp(d), dpp, vp(c), vp(g),
+                                                         ctypes.c_void_p(_stream(stream)))
+            self._check(code, "gna_chain_eval_general_host")
+            return c, g
         code = self._lib.gna_chain_eval_host(self._h, vp(p), vp(e), float(sigma), vp(d), dpp, vp(c), vp(g),
                                              vp(spectra_out), ctypes.c_void_p(_stream(stream)))
         self._check(code, "gna_chain_eval_host")
         return c, g
 
+    @property
+    def _npar(self) -> int:
+        return 4 if self.channel is None else 6
+
     def eval_host_async(self, params: np.ndarray, data: np.ndarray, eta: Optional[np.ndarray] = None,
                         sigma: float = 0.0, grad: bool = True, spectra: bool = False, stream=None) -> int:
         """Enqueues an evaluation from host buffers and returns a ticket at once
         (at most two outstanding); eval_host_wait(ticket) takes its results."""
-        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.npts, 4)
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.npts, self._npar)
         d = np.ascontiguousarray(data, dtype=np.float64)
         e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
         dpp = 1 if d.ndim == 2 else 0
         vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
         t = ctypes.c_int64(-1)
+        if self.channel is not None:
+            if spectra:
+                raise ValueError("the any-channel chain has no per-baseline spectra")
+            code = self._lib.gna_chain_eval_general_host_async(self._h, vp(p), vp(e), float(sigma), vp(d), dpp,
+                                                               int(bool(grad)), ctypes.c_void_p(_stream(stream)),
+                                                               ctypes.byref(t))
+            self._check(code, "gna_chain_eval_general_host_async")
+            return t.value
         code = self._lib.gna_chain_eval_host_async(self._h, vp(p), vp(e), float(sigma), vp(d), dpp, int(bool(grad)),
                                                    int(bool(spectra)), ctypes.c_void_p(_stream(stream)), ctypes.byref(t))
         self._check(code, "gna_chain_eval_host_async")
@@ -418,7 +471,7 @@ class Plan:
                        spectra_out: Optional[np.ndarray] = None):
         """Waits for the evaluation `ticket` and unpacks (chi2, grad) and, if given, the spectra."""
         c = chi2_out if chi2_out is not None else np.empty(self.npts)
-        g = grad_out if grad_out is not None else np.empty((self.npts, 4))
+        g = grad_out if grad_out is not None else np.empty((self.npts, self._npar))
         vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
         code = self._lib.gna_chain_eval_host_wait(self._h, ctypes.c_int64(ticket), vp(c), vp(g), vp(spectra_out))
         self._check(code, "gna_chain_eval_host_wait")
@@ -426,12 +479,20 @@ class Plan:
 
     def fit(self, params: torch.Tensor, data: torch.Tensor, iters: int = 20, lambda0: float = 1e-3,
             graph: bool = True, chi2_out: Optional[torch.Tensor] = None, stream=None):
-        """Batched Levenberg-Marquardt fits; params [npts, 4] is overwritten with the best points."""
+        """Batched Levenberg-Marquardt fits; params [npts, 4] ([npts, 6] on an
+        any-channel plan) float64 CUDA is overwritten with the best points."""
+        npar = self._npar
+        if params.dtype != torch.float64 or tuple(params.shape) != (self.npts, npar) or not params.is_contiguous():
+            raise ValueError("params must be a contiguous float64 tensor [npts, %d]" % npar)
+        if data.dtype != torch.float64 or tuple(data.shape) != (self.npts, self.nbins):
+            raise ValueError("data must be float64 [npts, nbins]")
         if chi2_out is None:
             chi2_out = self._out("fit_chi2", (self.npts,))
-        code = self._lib.gna_fit_batch(self._h, _ptr(params), _ptr(data), int(iters), float(lambda0), _ptr(chi2_out),
-                                       int(bool(graph)), ctypes.c_void_p(_stream(stream)))
-        self._check(code, "gna_fit_batch")
+        fn, what = ((self._lib.gna_fit_batch, "gna_fit_batch") if self.channel is None else
+                    (self._lib.gna_fit_batch_general, "gna_fit_batch_general"))
+        code = fn(self._h, _ptr(params), _ptr(data), int(iters), float(lambda0), _ptr(chi2_out), int(bool(graph)),
+                  ctypes.c_void_p(_stream(stream)))
+        self._check(code, what)
         return params, chi2_out
 
     def autotune(self, params: torch.Tensor, data: torch.Tensor, reps: int = 3, grad: bool = True,
@@ -538,33 +599,23 @@ class OscChi2(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, theta, eta, plan: Plan, data, sigma: float = 0.0):
-        if plan.npts != 1:
-            raise ValueError("OscChi2 works on a single-point plan")
-        npar = 4 if plan.channel is None else 6
-        p = theta.detach().reshape(1, npar).contiguous()
-        e = None if eta is None else eta.detach().contiguous()
-        # the library writes chi2 and the whole gradient [npar (+ nbins)]
-        # straight into the tensors this call returns and keeps (no copies)
-        chi2 = torch.empty((), dtype=torch.float64, device=p.device)
-        g = torch.empty(npar + (plan.nbins if e is not None else 0), dtype=torch.float64, device=p.device)
-        out = {"chi2": chi2, "grad": g[:npar]}
-        if e is not None:
-            out["grad_eta"] = g[npar:]
-        ev = plan.eval if plan.channel is None else plan.eval_general
-        ev(p, data, e, sigma, grad=True, grad_eta=e is not None, out=out)
-        ctx.npar = npar
-        ctx.save_for_backward(g)
-        ctx.has_eta = e is not None
-        ctx.shapes = (theta.shape, None if eta is None else eta.shape)
+        npar = plan._ad_check(theta, eta, data)
+        # the library writes chi2 and the gradient straight into the tensors
+        # this call returns and keeps (no copies); only pointers are read
+        # in the inputs' shapes, so that no view is needed; kept on ctx (an
+        # intermediate of this call: no saved-tensor bookkeeping)
+        chi2 = torch.empty((), dtype=torch.float64, device=theta.device)
+        ctx.g_theta = torch.empty(theta.shape, dtype=torch.float64, device=theta.device)
+        ctx.g_eta = None if eta is None else torch.empty(eta.shape, dtype=torch.float64, device=theta.device)
+        plan._eval_into(theta, data, eta, sigma, chi2, ctx.g_theta, ctx.g_eta)
         return chi2
 
     @staticmethod
     def backward(ctx, go):
-        (g,) = ctx.saved_tensors
-        h = go * g
-        ts, es = ctx.shapes
-        k = ctx.npar
-        return h[:k].view(ts), (h[k:].view(es) if ctx.has_eta else None), None, None, None
+        # fresh (non-view) tensors, which the gradient accumulation takes as
+        # they are instead of copying
+        ge = torch.mul(ctx.g_eta, go) if ctx.g_eta is not None else None
+        return torch.mul(ctx.g_theta, go), ge, None, None, None
 
 
 def chi2(theta, plan: Plan, data, eta=None, sigma: float = 0.0):

@@ -114,6 +114,8 @@ __global__ void k_prepare_general(const gna_osc_full* __restrict__ prm, int npts
                                   int anti, PointConst* __restrict__ out, GenConst* __restrict__ gout,
                                   int* __restrict__ zero, int64_t nz, int* __restrict__ status) {
     asm volatile("griddepcontrol.launch_dependents;");
+    // a programmatic dependent of the kernel before it: wait for it first
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t k = tid; k < nz; k += (int64_t)gridDim.x * blockDim.x) zero[k] = 0;
     const int p = (int)(tid / GNA_NLMAX), r = (int)(tid % GNA_NLMAX);
@@ -140,9 +142,16 @@ cudaError_t launch_prepare_general(const gna_osc_full* prm, int npts, const Base
                                    int anti, PointConst* out, GenConst* gout, int* zero, int64_t nz, int* status,
                                    cudaStream_t s) {
     const int64_t threads = std::max<int64_t>((int64_t)npts * GNA_NLMAX, std::min<int64_t>(nz, 1LL << 20));
-    k_prepare_general<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, alpha, beta, anti, out, gout,
-                                                                       zero, nz, status);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((threads + 255) / 256));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_prepare_general, prm, npts, bc, alpha, beta, anti, out, gout, zero, nz, status);
 }
 
 // ------------------------------------------------------------ launchers ----

@@ -55,6 +55,10 @@ struct GenConst {
 // Values per (point, bin) of the mixed node pass: U(3), V(3), [Y(3), Z(3)], Q(3).
 __host__ __device__ constexpr int gen_nv(bool grad) { return grad ? 15 : 9; }
 
+// Per-bin epilogue values: chi^2 term (1), with the gradient six more, and
+// for the fits the 21 entries of J^T W J (28 in all).
+constexpr int kGenNBVFit = 28;
+
 struct GenArgs {
     BinArgs b;
     const GenConst* gc;  // [npts]
@@ -228,29 +232,61 @@ __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int
         dM[5] = fmaf(c.af[2], vf[8], fmaf(0.5f * c.bf[2], vf[11], t31));
         const float gf = (float)(gd * f);
         for (int q = 0; q < 6; q++) regs[1 + q] = make_float2(gf * dM[q], 0.f);
+        if (a.NBV >= kGenNBVFit) {
+            // fits: this bin's part of J^T W J, J_q = d mu / d p_q, W = 2 / mu
+            const float ff = (float)f, h = 2.0f / (float)mu;
+            float J[6];
+            for (int q = 0; q < 6; q++) J[q] = ff * dM[q];
+            int t = 7;
+            for (int q = 0; q < 6; q++)
+                for (int r = q; r < 6; r++) regs[t++] = make_float2(h * J[q] * J[r], 0.f);
+        }
     }
     if (a.mu_out) a.mu_out[idx] = mu;
     if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
 }
 
-// Point p: lane l sums groups l, l + 32, ... in order, then one transposed
-// reduction; chi2 and the six-parameter gradient are written.
-__device__ inline void gen_point_reduce(const EpiArgs& a, int p, int lane) {
-    float2 v[16];
+// Group g of point p: lane l holds the values of bin 32 g + l in regs; up to
+// kGenNBVFit values, summed 16 at a time by transposed reductions (value
+// base + lane / 2 lands on the even lanes), stored per group.
+__device__ inline void gen_group_reduce(const EpiArgs& a, int p, int g, int lane, const float2* regs) {
+    const int i = (g << 5) + lane;
+    for (int base = 0; base < a.NBV; base += 16) {
+        float2 v[16];
 #pragma unroll
-    for (int j = 0; j < 16; j++) v[j] = make_float2(0.f, 0.f);
-    for (int g = lane; g < a.ngroups; g += 32) {
-        const float2* gv = a.gvals + ((int64_t)p * a.ngroups + g) * a.NBV;
-#pragma unroll
-        for (int j = 0; j < 7; j++)
-            if (j < a.NBV) v[j] = ff_add(v[j], __ldcg(gv + j));
+        for (int j = 0; j < 16; j++)
+            v[j] = (base + j < a.NBV && i < a.nbins) ? regs[base + j] : make_float2(0.f, 0.f);
+        warp_transpose_reduce<16>(v, lane);
+        const int vi = base + (lane >> 1);
+        if ((lane & 1) == 0 && vi < a.NBV) a.gvals[((int64_t)p * a.ngroups + g) * a.NBV + vi] = v[0];
     }
-    warp_transpose_reduce<16>(v, lane);
-    const int vi = lane >> 1;
-    if ((lane & 1) == 0 && vi < a.NBV) {
-        const double tot = (double)v[0].x + (double)v[0].y;
-        if (vi == 0) a.chi2[p] = tot;
-        else if (a.grad) a.grad[(int64_t)p * 6 + vi - 1] = tot;
+}
+
+// Point p: lane l sums groups l, l + 32, ... in order, then transposed
+// reductions, 16 values at a time; chi2, the six-parameter gradient and (fits)
+// the 21 entries of J^T W J are written.
+__device__ inline void gen_point_reduce(const EpiArgs& a, int p, int lane) {
+    for (int base = 0; base < a.NBV; base += 16) {
+        float2 v[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = make_float2(0.f, 0.f);
+        for (int g = lane; g < a.ngroups; g += 32) {
+            const float2* gv = a.gvals + ((int64_t)p * a.ngroups + g) * a.NBV + base;
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                if (base + j < a.NBV) v[j] = ff_add(v[j], __ldcg(gv + j));
+        }
+        warp_transpose_reduce<16>(v, lane);
+        const int vi = base + (lane >> 1);
+        if ((lane & 1) == 0 && vi < a.NBV) {
+            const double tot = (double)v[0].x + (double)v[0].y;
+            if (vi == 0) a.chi2[p] = tot;
+            else if (vi < 7) {
+                if (a.grad) a.grad[(int64_t)p * 6 + vi - 1] = tot;
+            } else if (a.H) {
+                a.H[(int64_t)p * 21 + vi - 7] = tot;
+            }
+        }
     }
 }
 
@@ -258,7 +294,7 @@ __device__ inline void gen_point_reduce(const EpiArgs& a, int p, int lane) {
 // sum the group, and the warp that completes the point's last group sums the
 // groups.
 static __device__ __noinline__ void gen_group_done(const EpiArgs& a, int p, int g, int lane, const float2* regs) {
-    group_reduce(a, p, g, lane, regs);
+    gen_group_reduce(a, p, g, lane, regs);
     __threadfence();
     __syncwarp();
     int lastp = 0;
@@ -335,7 +371,7 @@ __global__ void __launch_bounds__(256) k_fused_bins_gen(GenArgs ga) {
             continue;
         }
         const int i = b * 32 + lane;
-        float2 regs[15];
+        float2 regs[kGenNBVFit];
         if (i < a.nbins) {
             double vd[9];
             float vf[NV];
@@ -367,6 +403,8 @@ __global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __re
     const int g = pg - p * ea.ngroups;
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // the next evaluation's first kernel may be placed now (it waits for this one)
+    asm volatile("griddepcontrol.launch_dependents;");
     float2 acc[NVM];
 #pragma unroll
     for (int v = 0; v < NVM; v++) acc[v] = make_float2(0.f, 0.f);
@@ -405,7 +443,7 @@ __global__ void __launch_bounds__(W * 32) k_slices_reduce_gen(const float2* __re
             if (v < 6) vd[v] = (double)t.x + (double)t.y;
             else if (v >= NV - 3) vd[v - NV + 9] = (double)t.x + (double)t.y;  // Q
         }
-        float2 regs[15];
+        float2 regs[kGenNBVFit];
         if (i < ea.nbins) gen_bin_epilogue(ea, gc[p], p, i, vd, vf, in, regs);
         gen_group_done(ea, p, g, lane, regs);
     }
@@ -499,6 +537,12 @@ __device__ inline void gen_bin_epilogue64(const EpiArgs& a, const GenConst& c, i
         dM[4] = c.a[0] * v[6] + 0.5 * c.b[0] * v[9] + t31;
         dM[5] = c.a[2] * v[8] + 0.5 * c.b[2] * v[11] + t31;
         for (int q = 0; q < 6; q++) regs[1 + q] = to_ff(gd * f * dM[q]);
+        if (a.NBV >= kGenNBVFit) {  // fits: J^T W J, J_q = d mu / d p_q = f dM_q, W = 2 / mu
+            const double h = 2.0 / mu;
+            int t = 7;
+            for (int q = 0; q < 6; q++)
+                for (int r = q; r < 6; r++) regs[t++] = to_ff(h * (f * dM[q]) * (f * dM[r]));
+        }
     }
     if (a.mu_out) a.mu_out[idx] = mu;
     if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
@@ -532,7 +576,7 @@ __global__ void __launch_bounds__(256) k_fused64_bins_gen(GenArgs64 ga) {
         const double2* g = a.grid + a.goff[gi] + (int64_t)b * n * 32 + lane;
         for (int k = 0; k < n; k++) m.update(g[(int64_t)k * 32], acc);
         const int i = b * 32 + lane;
-        float2 regs[15];
+        float2 regs[kGenNBVFit];
         if (i < a.nbins) gen_bin_epilogue64(a.ea, ga.gc[p], p, i, acc, NV, bin_inputs(a.ea, p, i), regs);
         gen_group_done(a.ea, p, b, lane, regs);
     }

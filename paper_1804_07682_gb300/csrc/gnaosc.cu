@@ -146,6 +146,7 @@ struct gna_plan {
     double* d_plainDmu = nullptr;
     // fitter
     LMState* d_lm = nullptr;
+    LMStateT<6>* d_lm6 = nullptr;  // any-channel plans: six parameters
     // launch shape
     int block = kDefaultBlock, npt = kDefaultNodesPerThread, grid_mult = 0;
     int slice_len = 0;  // slice mapping: nodes per slice (0: chosen from the GPU size)
@@ -335,7 +336,8 @@ struct EvalReq {
     double* grad_eta;  // [npts][nbins] or NULL
     double* mu;
     double* spectra;
-    double* H;  // [npts][10] or NULL (fitter)
+    double* H;  // [npts][10] (survival chain) or [npts][21] (any channel), or NULL (fitter)
+    const gna_osc_full* pfull = nullptr;  // any-channel plans: [npts] parameters
 };
 
 // Epilogue arguments of one evaluation (outputs of q; NV node sums per bin
@@ -457,6 +459,46 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
         plan->cache_spec = spec;
     }
     *launches = nl;
+    return GNA_OK;
+}
+
+// Enqueue one evaluation of an any-channel plan (q.pfull: the parameters;
+// q.H set for the fits' J^T W J); counts kernel launches into *launches.
+gna_status enqueue_eval_general(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* launches) {
+    const bool grad = q.grad || q.grad_eta || q.H;
+    const int NV = gen_nv(grad);
+    SliceShape ssh{1, 0, plan->ntasks};
+    if (plan->mapping == MAP_SLICES) {
+        ssh = slice_shape(plan);
+        if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
+    }
+    const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups);
+    CU(launch_prepare_general(q.pfull, plan->npts, plan->bc, plan->g_alpha, plan->g_beta, plan->g_anti, plan->d_pc,
+                              plan->d_gc, plan->d_counters, ncnt, plan->d_status, s));
+    EpiArgs ea = make_epi(plan, q, grad, false, NV);
+    ea.NBV = q.H ? kGenNBVFit : (grad ? 7 : 1);  // chi2, the six-parameter gradient terms, J^T W J
+    ea.binsums = nullptr;
+    const bool sliced = ssh.S > 1;
+    int64_t g = (int64_t)plan->sm_count * general_resident_ctas(plan->ph, plan->nl_inst, grad, plan->block);
+    g = std::max<int64_t>(1, std::min<int64_t>(g, ((int64_t)ssh.ntasks * 32 + plan->block - 1) / plan->block));
+    if (plan->ph == 2) {
+        GenArgs64 ga64{BinArgs64{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, plan->ntasks,
+                                 plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea},
+                       plan->d_gc};
+        CU(dispatch_general64(plan->nl_inst, grad, ga64, (int)g, plan->block, s));
+        *launches = 2;
+        return GNA_OK;
+    }
+    GenArgs ga{BinArgs{plan->grid_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, ssh.ntasks,
+                       plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, ssh.S, ssh.L,
+                       sliced ? plan->d_slices : nullptr},
+               plan->d_gc};
+    CU(dispatch_general(plan->ph, plan->nl_inst, grad, ga, (int)g, plan->block, s));
+    *launches = 2;
+    if (sliced) {
+        CU(launch_slices_reduce_general(plan->d_slices, ssh.S, NV, ea, plan->d_gc, plan->npts, s));
+        *launches = 3;
+    }
     return GNA_OK;
 }
 
@@ -1015,16 +1057,19 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         if (plan->slices_cap > 1)
             TRY(dalloc(plan, &plan->d_slices, (size_t)pg * plan->slices_cap * nv_max * 32));
     }
-    TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * 15));
-    TRY(dalloc(plan, &plan->d_gvals, (size_t)d->npts * ngroups * 15));
+    const int nbv_max = plan->general ? kGenNBVFit : 15;
+    TRY(dalloc(plan, &plan->d_binvals, (size_t)d->npts * d->nbins * nbv_max));
+    TRY(dalloc(plan, &plan->d_gvals, (size_t)d->npts * ngroups * nbv_max));
     if (!plan->general && (int64_t)d->npts * d->nbins * nv_max <= (32LL << 20))  // up to 256 MB
         TRY(dalloc(plan, &plan->d_binsums, (size_t)d->npts * d->nbins * nv_max));
-    TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * 10));
+    const int npar = plan->general ? 6 : 4;
+    TRY(dalloc(plan, &plan->d_H, (size_t)d->npts * (npar * (npar + 1) / 2)));
     TRY(dalloc(plan, &plan->d_chi2_tmp, d->npts));
-    TRY(dalloc(plan, &plan->d_grad_tmp, (size_t)d->npts * 4));
-    plan->in_cap = (size_t)d->npts * 4 + (size_t)plan->max_datasets * d->nbins + d->nbins;
-    plan->out_cap = (size_t)d->npts * 5;
-    if ((int64_t)d->npts * d->nL * d->nbins <= (1LL << 24)) plan->out_cap += (size_t)d->npts * d->nL * d->nbins;
+    TRY(dalloc(plan, &plan->d_grad_tmp, (size_t)d->npts * npar));
+    plan->in_cap = (size_t)d->npts * npar + (size_t)plan->max_datasets * d->nbins + d->nbins;
+    plan->out_cap = (size_t)d->npts * (1 + npar);
+    if (!plan->general && (int64_t)d->npts * d->nL * d->nbins <= (1LL << 24))
+        plan->out_cap += (size_t)d->npts * d->nL * d->nbins;
     CU(cudaStreamCreateWithFlags(&plan->cp_in, cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&plan->cp_out, cudaStreamNonBlocking));
     for (auto& h : plan->hs) {
@@ -1039,7 +1084,8 @@ static gna_status plan_build(gna_plan* plan, const gna_plan_desc* d, cudaStream_
         for (cudaEvent_t* ev : {&h.in_ready, &h.computed, &h.done})
             CU(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
     }
-    TRY(dalloc(plan, &plan->d_lm, d->npts));
+    if (plan->general) TRY(dalloc(plan, &plan->d_lm6, d->npts));
+    else TRY(dalloc(plan, &plan->d_lm, d->npts));
     TRY(dalloc(plan, &plan->d_status, 1));
     CU(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
     if (want_plain) {
@@ -1183,43 +1229,9 @@ gna_status gna_chain_eval_general(gna_plan* plan, const gna_osc_full* params, co
         return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
-    const bool grad = out->grad || out->grad_eta;
-    const int NV = gen_nv(grad);
-    SliceShape ssh{1, 0, plan->ntasks};
-    if (plan->mapping == MAP_SLICES) {
-        ssh = slice_shape(plan);
-        if ((int64_t)plan->npts * plan->ngroups * ssh.S >= (1LL << 31)) return fail(plan, GNA_ESHAPE, "too many slice tasks");
-    }
-    const int64_t ncnt = 1 + (int64_t)plan->npts * (1 + plan->ngroups);
-    CU(launch_prepare_general(params, plan->npts, plan->bc, plan->g_alpha, plan->g_beta, plan->g_anti, plan->d_pc,
-                              plan->d_gc, plan->d_counters, ncnt, plan->d_status, s));
     EvalReq q{nullptr, eta, sigma_eta, data, data_per_point, out->chi2, out->grad, out->grad_eta, out->mu, nullptr,
-              nullptr};
-    EpiArgs ea = make_epi(plan, q, grad, false, NV);
-    ea.NBV = grad ? 7 : 1;  // chi2 and the six-parameter gradient terms
-    ea.binsums = nullptr;
-    const bool sliced = ssh.S > 1;
-    int64_t g = (int64_t)plan->sm_count * general_resident_ctas(plan->ph, plan->nl_inst, grad, plan->block);
-    g = std::max<int64_t>(1, std::min<int64_t>(g, ((int64_t)ssh.ntasks * 32 + plan->block - 1) / plan->block));
-    if (plan->ph == 2) {
-        GenArgs64 ga64{BinArgs64{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, plan->ntasks,
-                                 plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea},
-                       plan->d_gc};
-        CU(dispatch_general64(plan->nl_inst, grad, ga64, (int)g, plan->block, s));
-        plan->last_launches = 2;
-        return GNA_OK;
-    }
-    GenArgs ga{BinArgs{plan->grid_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, ssh.ntasks,
-                       plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, ssh.S, ssh.L,
-                       sliced ? plan->d_slices : nullptr},
-               plan->d_gc};
-    CU(dispatch_general(plan->ph, plan->nl_inst, grad, ga, (int)g, plan->block, s));
-    plan->last_launches = 2;
-    if (sliced) {
-        CU(launch_slices_reduce_general(plan->d_slices, ssh.S, NV, ea, plan->d_gc, plan->npts, s));
-        plan->last_launches = 3;
-    }
-    return GNA_OK;
+              nullptr, params};
+    return enqueue_eval_general(plan, q, s, &plan->last_launches);
 }
 
 gna_status gna_chain_eval_cached(gna_plan* plan, const double* eta, double sigma_eta, const double* data,
@@ -1248,16 +1260,20 @@ gna_status gna_chain_eval_cached(gna_plan* plan, const double* eta, double sigma
     return GNA_OK;
 }
 
-gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
-                                     const double* data, int data_per_point, int grad, int spectra, void* stream,
-                                     int64_t* ticket) {
-    if (!plan) return GNA_EINVAL;
-    if (plan->general) return fail(plan, GNA_ESTATE, "not available for an any-channel plan");
+}  // extern "C"
+
+namespace {
+
+// Host-buffer evaluation of either chain: params are npar doubles per point
+// (gna_osc, or gna_osc_full on an any-channel plan).
+gna_status host_async(gna_plan* plan, const double* params, const double* eta, double sigma_eta, const double* data,
+                      int data_per_point, int grad, int spectra, void* stream, int64_t* ticket) {
+    const int npar = plan->general ? 6 : 4;
     if (!params || !data || !ticket) return fail(plan, GNA_EINVAL, "params, data and ticket are required");
     if (data_per_point && plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "data_per_point needs max_datasets >= npts");
     const size_t n_spec = (size_t)plan->npts * plan->nL * plan->nbins;
-    if (spectra && plan->out_cap < (size_t)plan->npts * 5 + n_spec)
-        return fail(plan, GNA_ESHAPE, "spectra staging exceeds 2^24 values");
+    const size_t n_head = (size_t)plan->npts * (1 + npar);  // chi2, gradient
+    if (spectra && plan->out_cap < n_head + n_spec) return fail(plan, GNA_ESHAPE, "spectra staging exceeds 2^24 values");
     const int64_t t = plan->next_ticket;
     auto& h = plan->hs[t & 1];
     if (h.pending) return fail(plan, GNA_ESTATE, "two host evaluations are outstanding: wait for ticket %lld first", (long long)h.ticket);
@@ -1266,20 +1282,20 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
     // the slot's previous evaluation was taken; its copy from h_in is complete
     CU(cudaEventSynchronize(h.done));
     // pack the inputs into pinned staging: [params | data | eta]
-    const size_t n_par = (size_t)plan->npts * 4;
+    const size_t n_par = (size_t)plan->npts * npar;
     const size_t n_dat = (data_per_point ? (size_t)plan->npts : 1) * plan->nbins;
     const size_t n_eta = eta ? (size_t)plan->nbins : 0;
     memcpy(h.h_in, params, n_par * sizeof(double));
     memcpy(h.h_in + n_par, data, n_dat * sizeof(double));
     if (eta) memcpy(h.h_in + n_par + n_dat, eta, n_eta * sizeof(double));
     const size_t n_in = n_par + n_dat + n_eta;
-    const size_t n_out = (size_t)plan->npts * 5 + (spectra ? n_spec : 0);
+    const size_t n_out = n_head + (spectra ? n_spec : 0);
     double* d_par = h.d_in;
     double* d_dat = h.d_in + n_par;
     double* d_eta = eta ? h.d_in + n_par + n_dat : nullptr;
-    EvalReq q{(const gna_osc*)d_par, d_eta, sigma_eta, d_dat, data_per_point, h.d_out,
-              grad ? h.d_out + plan->npts : nullptr, nullptr, nullptr,
-              spectra ? h.d_out + (size_t)plan->npts * 5 : nullptr, nullptr};
+    EvalReq q{plan->general ? nullptr : (const gna_osc*)d_par, d_eta, sigma_eta, d_dat, data_per_point, h.d_out,
+              grad ? h.d_out + plan->npts : nullptr, nullptr, nullptr, spectra ? h.d_out + n_head : nullptr, nullptr,
+              plan->general ? (const gna_osc_full*)d_par : nullptr};
     // upload on cp_in once the evaluation that last read this slot's inputs
     // is done; it overlaps whatever the caller's stream is running
     CU(cudaStreamWaitEvent(plan->cp_in, h.computed, 0));
@@ -1289,7 +1305,9 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
     // download of this slot's previous results
     CU(cudaStreamWaitEvent(s, h.in_ready, 0));
     CU(cudaStreamWaitEvent(s, h.done, 0));
-    auto enqueue_all = [&](cudaStream_t st, int* nl) -> gna_status { return enqueue_eval(plan, q, st, nl); };
+    auto enqueue_all = [&](cudaStream_t st, int* nl) -> gna_status {
+        return plan->general ? enqueue_eval_general(plan, q, st, nl) : enqueue_eval(plan, q, st, nl);
+    };
     if (plan->use_graph) {
         double sig = sigma_eta;
         uintptr_t sigbits;
@@ -1341,6 +1359,26 @@ gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, cons
     return GNA_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+gna_status gna_chain_eval_host_async(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
+                                     const double* data, int data_per_point, int grad, int spectra, void* stream,
+                                     int64_t* ticket) {
+    if (!plan) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "an any-channel plan is evaluated by gna_chain_eval_general_host_async");
+    return host_async(plan, (const double*)params, eta, sigma_eta, data, data_per_point, grad, spectra, stream, ticket);
+}
+
+gna_status gna_chain_eval_general_host_async(gna_plan* plan, const gna_osc_full* params, const double* eta,
+                                             double sigma_eta, const double* data, int data_per_point, int grad,
+                                             void* stream, int64_t* ticket) {
+    if (!plan) return GNA_EINVAL;
+    if (!plan->general) return fail(plan, GNA_ESTATE, "the plan was created for the nue_bar survival chain");
+    return host_async(plan, (const double*)params, eta, sigma_eta, data, data_per_point, grad, 0, stream, ticket);
+}
+
 gna_status gna_chain_eval_host_wait(gna_plan* plan, int64_t ticket, double* chi2, double* grad, double* spectra) {
     if (!plan) return GNA_EINVAL;
     if (ticket < 0) return fail(plan, GNA_EINVAL, "bad ticket");
@@ -1348,10 +1386,23 @@ gna_status gna_chain_eval_host_wait(gna_plan* plan, int64_t ticket, double* chi2
     if (h.ticket != ticket || !h.pending) return fail(plan, GNA_ESTATE, "no outstanding host evaluation %lld", (long long)ticket);
     CU(cudaEventSynchronize(h.done));
     h.pending = false;
+    const int npar = plan->general ? 6 : 4;
     if (chi2) memcpy(chi2, h.h_out, sizeof(double) * plan->npts);
-    if (grad && h.grad) memcpy(grad, h.h_out + plan->npts, sizeof(double) * 4 * plan->npts);
-    if (spectra && h.spectra) memcpy(spectra, h.h_out + (size_t)plan->npts * 5, sizeof(double) * plan->npts * plan->nL * plan->nbins);
+    if (grad && h.grad) memcpy(grad, h.h_out + plan->npts, sizeof(double) * npar * plan->npts);
+    if (spectra && h.spectra)
+        memcpy(spectra, h.h_out + (size_t)plan->npts * (1 + npar), sizeof(double) * plan->npts * plan->nL * plan->nbins);
     return GNA_OK;
+}
+
+gna_status gna_chain_eval_general_host(gna_plan* plan, const gna_osc_full* params, const double* eta,
+                                       double sigma_eta, const double* data, int data_per_point, double* chi2,
+                                       double* grad, void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (!chi2) return fail(plan, GNA_EINVAL, "params, data and chi2 are required");
+    int64_t t = -1;
+    TRY(gna_chain_eval_general_host_async(plan, params, eta, sigma_eta, data, data_per_point, grad != nullptr, stream,
+                                          &t));
+    return gna_chain_eval_host_wait(plan, t, chi2, grad, nullptr);
 }
 
 gna_status gna_chain_eval_host(gna_plan* plan, const gna_osc* params, const double* eta, double sigma_eta,
@@ -1421,26 +1472,34 @@ gna_status gna_chain_eval_plain(gna_plan* plan, const gna_osc* params, const dou
     return GNA_OK;
 }
 
-gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, int iters, double lambda0, double* chi2_out,
-                         int use_graph, void* stream) {
-    if (!plan) return GNA_EINVAL;
-    if (plan->general) return fail(plan, GNA_ESTATE, "not available for an any-channel plan");
+}  // extern "C"
+
+namespace {
+
+// Batched Levenberg-Marquardt fits of either chain: NP parameters per data set
+// (NP doubles per point: gna_osc, or gna_osc_full on an any-channel plan).
+template <int NP>
+gna_status fit_impl(gna_plan* plan, double* params, const double* data, int iters, double lambda0, double* chi2_out,
+                    int use_graph, cudaStream_t s, LMStateT<NP>* lm) {
     if (!params || !data || !chi2_out) return fail(plan, GNA_EINVAL, "params, data and chi2_out are required");
     if (iters < 1) return fail(plan, GNA_EINVAL, "iters must be >= 1");
     if (plan->max_datasets < plan->npts) return fail(plan, GNA_ESHAPE, "fits need one data row per point");
-    cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
-    CU(launch_lm_init(plan->d_lm, plan->npts, lambda0, s));
-    EvalReq q{params, nullptr, 0.0, data, 1, plan->d_chi2_tmp, plan->d_grad_tmp, nullptr, nullptr, nullptr, plan->d_H};
+    CU(launch_lm_init<NP>(lm, plan->npts, lambda0, s));
+    EvalReq q{NP == 4 ? (const gna_osc*)params : nullptr, nullptr, 0.0, data, 1, plan->d_chi2_tmp, plan->d_grad_tmp,
+              nullptr, nullptr, nullptr, plan->d_H, NP == 6 ? (const gna_osc_full*)params : nullptr};
+    auto enqueue = [&](cudaStream_t st, int* nl) -> gna_status {
+        return NP == 6 ? enqueue_eval_general(plan, q, st, nl) : enqueue_eval(plan, q, st, nl);
+    };
     int launches = 1;
     if (use_graph) {
         cudaStream_t cs = plan->cap_stream;
         cudaGraph_t g = nullptr;
         CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         int nl = 0;
-        gna_status st = enqueue_eval(plan, q, cs, &nl);
-        cudaError_t e1 = launch_lm_update(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, plan->d_lm, params,
-                                          chi2_out, cs);
+        gna_status st = enqueue(cs, &nl);
+        cudaError_t e1 = launch_lm_update<NP>(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, lm, params,
+                                              chi2_out, cs);
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (st != GNA_OK || e1 != cudaSuccess || e != cudaSuccess) {
             cudaGetLastError();
@@ -1465,14 +1524,34 @@ gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, in
     } else {
         for (int it = 0; it < iters; it++) {
             int nl = 0;
-            TRY(enqueue_eval(plan, q, s, &nl));
-            CU(launch_lm_update(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, plan->d_lm, params, chi2_out, s));
+            TRY(enqueue(s, &nl));
+            CU(launch_lm_update<NP>(plan->npts, plan->d_chi2_tmp, plan->d_grad_tmp, plan->d_H, lm, params, chi2_out, s));
             launches += nl + 1;
         }
     }
-    CU(launch_lm_finish(plan->npts, plan->d_lm, params, s));
+    CU(launch_lm_finish<NP>(plan->npts, lm, params, s));
     plan->last_launches = launches + 1;
     return GNA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gna_status gna_fit_batch(gna_plan* plan, gna_osc* params, const double* data, int iters, double lambda0, double* chi2_out,
+                         int use_graph, void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (plan->general) return fail(plan, GNA_ESTATE, "an any-channel plan is fitted by gna_fit_batch_general");
+    return fit_impl<4>(plan, (double*)params, data, iters, lambda0, chi2_out, use_graph, (cudaStream_t)stream,
+                       plan->d_lm);
+}
+
+gna_status gna_fit_batch_general(gna_plan* plan, gna_osc_full* params, const double* data, int iters, double lambda0,
+                                 double* chi2_out, int use_graph, void* stream) {
+    if (!plan) return GNA_EINVAL;
+    if (!plan->general) return fail(plan, GNA_ESTATE, "the plan was created for the nue_bar survival chain");
+    return fit_impl<6>(plan, (double*)params, data, iters, lambda0, chi2_out, use_graph, (cudaStream_t)stream,
+                       plan->d_lm6);
 }
 
 gna_status gna_plan_get_tuning(const gna_plan* plan, char* buf, int buflen) {

@@ -24,6 +24,10 @@ namespace gna {
 __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, BaseConst bc, PointConst* __restrict__ out,
                                  int* __restrict__ zero, int64_t nz, int* __restrict__ status) {
     asm volatile("griddepcontrol.launch_dependents;");
+    // launched as a programmatic dependent of the kernel before it (that
+    // kernel's launch latency is hidden): wait until it has completed and its
+    // writes are visible before touching the counters and constants it may use
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t k = tid; k < nz; k += (int64_t)gridDim.x * blockDim.x) zero[k] = 0;
     const int64_t idx = tid;
@@ -72,8 +76,16 @@ __global__ void k_prepare_points(const gna_osc* __restrict__ prm, int npts, Base
 cudaError_t launch_prepare(const gna_osc* prm, int npts, const BaseConst& bc, PointConst* out, cudaStream_t s,
                            int* zero, int64_t nz, int* status) {
     const int64_t threads = std::max<int64_t>((int64_t)npts * GNA_NLMAX, std::min<int64_t>(nz, 1LL << 20));
-    k_prepare_points<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(prm, npts, bc, out, zero, nz, status);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((threads + 255) / 256));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_prepare_points, prm, npts, bc, out, zero, nz, status);
 }
 
 // --------------------------------------------------------------- step a1 --
@@ -418,121 +430,147 @@ cudaError_t launch_oscprob(const double* E, int64_t n, const OscConst& oc, int p
     return cudaGetLastError();
 }
 
-// ------------------------------------------------ Levenberg-Marquardt ----
-// Per dataset: accept the evaluated trial if chi2 improved (lambda /= 10)
-// else reject it (lambda *= 10); solve (H + lambda diag H) delta = -g at the
-// best point (Gaussian elimination, partial pivoting) and clamp the next trial.
-__global__ void k_lm_init(LMState* __restrict__ st, int npts, double lam0) {
+// ------------------------------------------------------------- step a11 --
+// Batched Levenberg-Marquardt, one thread per data set, NP = 4 (survival
+// chain: s2_12, s2_13, dm2_21, dm2_32) or 6 (any channel: s2_12, s2_13,
+// s2_23, delta_cp, dm2_21, dm2_32).  The parameters are NP consecutive doubles
+// per point (the layout of gna_osc and of gna_osc_full).
+template <int NP>
+__global__ void k_lm_init(LMStateT<NP>* __restrict__ st, int npts, double lam0) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts) return;
-    LMState s;
-    for (int q = 0; q < 4; q++) {
+    LMStateT<NP> s;
+    for (int q = 0; q < NP; q++) {
         s.best[q] = 0.0;
         s.g[q] = 0.0;
     }
-    for (int q = 0; q < 10; q++) s.H[q] = 0.0;
+    for (int q = 0; q < NP * (NP + 1) / 2; q++) s.H[q] = 0.0;
     s.chi2 = HUGE_VAL;
     s.lam = lam0;
     st[p] = s;
 }
 
+// Box of the trials: mixing parameters (sin^2) in [1e-6, 1 - 1e-6], mass
+// splittings >= 1e-7 eV^2, delta_cp free.
+template <int NP>
+__device__ __forceinline__ void lm_box(int q, double& lo, double& hi) {
+    const bool mix = (NP == 4) ? q < 2 : q < 3;
+    const bool cp = (NP == 6) && q == 3;
+    lo = mix ? 1e-6 : cp ? -HUGE_VAL : 1e-7;
+    hi = mix ? 1.0 - 1e-6 : HUGE_VAL;
+}
+
+// One iteration per data set: accept the trial just evaluated if its chi^2
+// improved on the best (lambda / 10) else reject it (lambda x 10); solve
+// (H + lambda diag H) delta = -g at the best point (Gaussian elimination with
+// partial pivoting, FP64) and write the next trial, clamped into the box.
+template <int NP>
 __global__ void k_lm_update(int npts, const double* __restrict__ chi2, const double* __restrict__ grad,
-                            const double* __restrict__ H, LMState* __restrict__ st, gna_osc* __restrict__ prm,
+                            const double* __restrict__ H, LMStateT<NP>* __restrict__ st, double* __restrict__ prm,
                             double* __restrict__ chi2_best) {
+    constexpr int NH = NP * (NP + 1) / 2;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts) return;
-    LMState s = st[p];
-    const gna_osc t = prm[p];
-    const double th[4] = {t.s2_12, t.s2_13, t.dm2_21, t.dm2_32};
+    LMStateT<NP> s = st[p];
+    double* th = prm + (int64_t)p * NP;
     const double c = chi2[p];
     if (c < s.chi2) {
         s.chi2 = c;
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < NP; q++) {
             s.best[q] = th[q];
-            s.g[q] = grad[(int64_t)p * 4 + q];
+            s.g[q] = grad[(int64_t)p * NP + q];
         }
-        for (int q = 0; q < 10; q++) s.H[q] = H[(int64_t)p * 10 + q];
+        for (int q = 0; q < NH; q++) s.H[q] = H[(int64_t)p * NH + q];
         s.lam = s.lam / 10.0;
     } else {
         s.lam = s.lam * 10.0;
     }
-    double A[4][5];
-    int t10 = 0;
-    for (int q = 0; q < 4; q++)
-        for (int r = q; r < 4; r++) {
-            A[q][r] = s.H[t10];
-            A[r][q] = s.H[t10];
-            t10++;
+    double A[NP][NP + 1];
+    int t = 0;
+    for (int q = 0; q < NP; q++)
+        for (int r = q; r < NP; r++) {
+            A[q][r] = s.H[t];
+            A[r][q] = s.H[t];
+            t++;
         }
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < NP; q++) {
         A[q][q] += s.lam * A[q][q];
-        A[q][4] = -s.g[q];
+        A[q][NP] = -s.g[q];
     }
     bool ok = true;
-    for (int col = 0; col < 4; col++) {
+    for (int col = 0; col < NP; col++) {
         int piv = col;
-        for (int r = col + 1; r < 4; r++)
+        for (int r = col + 1; r < NP; r++)
             if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
         if (!(fabs(A[piv][col]) > 0.0)) {
             ok = false;
             break;
         }
         if (piv != col)
-            for (int j = 0; j < 5; j++) {
+            for (int j = 0; j <= NP; j++) {
                 const double tmp = A[col][j];
                 A[col][j] = A[piv][j];
                 A[piv][j] = tmp;
             }
-        for (int r = col + 1; r < 4; r++) {
+        for (int r = col + 1; r < NP; r++) {
             const double m = A[r][col] / A[col][col];
-            for (int j = col; j < 5; j++) A[r][j] -= m * A[col][j];
+            for (int j = col; j <= NP; j++) A[r][j] -= m * A[col][j];
         }
     }
-    double delta[4] = {0, 0, 0, 0};
+    double delta[NP];
+    for (int q = 0; q < NP; q++) delta[q] = 0.0;
     if (ok)
-        for (int q = 3; q >= 0; q--) {
-            double acc = A[q][4];
-            for (int j = q + 1; j < 4; j++) acc -= A[q][j] * delta[j];
+        for (int q = NP - 1; q >= 0; q--) {
+            double acc = A[q][NP];
+            for (int j = q + 1; j < NP; j++) acc -= A[q][j] * delta[j];
             delta[q] = acc / A[q][q];
         }
-    const double lo[4] = {1e-6, 1e-6, 1e-7, 1e-7};
-    const double hi[4] = {1.0 - 1e-6, 1.0 - 1e-6, HUGE_VAL, HUGE_VAL};
-    double nx[4];
-    for (int q = 0; q < 4; q++) nx[q] = fmin(fmax(s.best[q] + delta[q], lo[q]), hi[q]);
-    prm[p].s2_12 = nx[0];
-    prm[p].s2_13 = nx[1];
-    prm[p].dm2_21 = nx[2];
-    prm[p].dm2_32 = nx[3];
+    for (int q = 0; q < NP; q++) {
+        double lo, hi;
+        lm_box<NP>(q, lo, hi);
+        th[q] = fmin(fmax(s.best[q] + delta[q], lo), hi);
+    }
     st[p] = s;
     if (chi2_best) chi2_best[p] = s.chi2;
 }
 
-__global__ void k_lm_finish(int npts, const LMState* __restrict__ st, gna_osc* __restrict__ prm) {
+template <int NP>
+__global__ void k_lm_finish(int npts, const LMStateT<NP>* __restrict__ st, double* __restrict__ prm) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts) return;
-    prm[p].s2_12 = st[p].best[0];
-    prm[p].s2_13 = st[p].best[1];
-    prm[p].dm2_21 = st[p].best[2];
-    prm[p].dm2_32 = st[p].best[3];
+    for (int q = 0; q < NP; q++) prm[(int64_t)p * NP + q] = st[p].best[q];
 }
 
-cudaError_t launch_lm_init(LMState* st, int npts, double lam0, cudaStream_t s) {
-    k_lm_init<<<(npts + 127) / 128, 128, 0, s>>>(st, npts, lam0);
+template <int NP>
+cudaError_t launch_lm_init(LMStateT<NP>* st, int npts, double lam0, cudaStream_t s) {
+    k_lm_init<NP><<<(npts + 127) / 128, 128, 0, s>>>(st, npts, lam0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMState* st, gna_osc* prm,
-                             double* chi2_best, cudaStream_t s) {
-    k_lm_update<<<(npts + 127) / 128, 128, 0, s>>>(npts, chi2, grad, H, st, prm, chi2_best);
+template <int NP>
+cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMStateT<NP>* st,
+                             double* prm, double* chi2_best, cudaStream_t s) {
+    k_lm_update<NP><<<(npts + 127) / 128, 128, 0, s>>>(npts, chi2, grad, H, st, prm, chi2_best);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lm_finish(int npts, const LMState* st, gna_osc* prm, cudaStream_t s) {
-    k_lm_finish<<<(npts + 127) / 128, 128, 0, s>>>(npts, st, prm);
+template <int NP>
+cudaError_t launch_lm_finish(int npts, const LMStateT<NP>* st, double* prm, cudaStream_t s) {
+    k_lm_finish<NP><<<(npts + 127) / 128, 128, 0, s>>>(npts, st, prm);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_lm_init<4>(LMStateT<4>*, int, double, cudaStream_t);
+template cudaError_t launch_lm_init<6>(LMStateT<6>*, int, double, cudaStream_t);
+template cudaError_t launch_lm_update<4>(int, const double*, const double*, const double*, LMStateT<4>*, double*,
+                                         double*, cudaStream_t);
+template cudaError_t launch_lm_update<6>(int, const double*, const double*, const double*, LMStateT<6>*, double*,
+                                         double*, cudaStream_t);
+template cudaError_t launch_lm_finish<4>(int, const LMStateT<4>*, double*, cudaStream_t);
+template cudaError_t launch_lm_finish<6>(int, const LMStateT<6>*, double*, cudaStream_t);
 
 }  // namespace gna
+
 
 namespace gna {
 

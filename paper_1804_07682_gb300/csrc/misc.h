@@ -67,13 +67,16 @@ struct OscGenConst {
 };
 cudaError_t launch_oscgen(const double* E, int64_t n, const OscGenConst& oc, int prec, void* P, cudaStream_t s);
 
-struct LMState {
-    double best[4];
+// Levenberg-Marquardt state of one data set for NP parameters.
+template <int NP>
+struct LMStateT {
+    double best[NP];
     double chi2;
-    double g[4];
-    double H[10];
+    double g[NP];
+    double H[NP * (NP + 1) / 2];
     double lam;
 };
+using LMState = LMStateT<4>;
 
 // Per-point constants (step a0); also zeroes nz ints at zero (the evaluation's
 // counters) and sets *status to GNA_EINVAL for a point outside the physical domain.
@@ -87,10 +90,13 @@ cudaError_t launch_sum_weights(const float4* grid, int nbins, int n, int layout,
 // weights, bin integration, chi^2 (4 launches, 6 with the tangents).
 cudaError_t launch_plain_chunk(const PlainArgs& a, const PlainChi2Args& ca, cudaStream_t s);
 cudaError_t launch_oscprob(const double* E, int64_t n, const OscConst& oc, int prec, void* P, cudaStream_t s);
-cudaError_t launch_lm_init(LMState* st, int npts, double lam0, cudaStream_t s);
-cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMState* st, gna_osc* prm,
-                             double* chi2_best, cudaStream_t s);
+template <int NP>
+cudaError_t launch_lm_init(LMStateT<NP>* st, int npts, double lam0, cudaStream_t s);
+template <int NP>
+cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMStateT<NP>* st,
+                             double* prm, double* chi2_best, cudaStream_t s);
 cudaError_t launch_fma_probe(int blocks, int iters, float* out, cudaStream_t s);
-cudaError_t launch_lm_finish(int npts, const LMState* st, gna_osc* prm, cudaStream_t s);
+template <int NP>
+cudaError_t launch_lm_finish(int npts, const LMStateT<NP>* st, double* prm, cudaStream_t s);
 
 }  // namespace gna

@@ -26,6 +26,9 @@ __global__ void __launch_bounds__(W * 32) k_slices_reduce(const float2* __restri
     const int g = pg - p * ea.ngroups;
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // the next evaluation's first kernel may be placed now; it waits for this
+    // kernel to complete before it touches anything
+    asm volatile("griddepcontrol.launch_dependents;");
     float2 acc[NVM];
 #pragma unroll
     for (int v = 0; v < NVM; v++) acc[v] = make_float2(0.f, 0.f);

@@ -822,3 +822,70 @@ def test_general_chain_through_autograd(api):
     assert normrel(th.grad.cpu().numpy(), 3.0 * ref["grad"][:6]) < 1e-9
     assert normrel(et.grad.cpu().numpy(), 3.0 * ref["grad"][6:]) < 1e-9
     plan.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_general_chain_from_host_buffers(api, graph):
+    # the any-channel chain from host buffers (one packed copy in, one out):
+    # the device call's results bit for bit, two evaluations in flight, and
+    # the survival chain's host calls refuse the plan
+    from paper_1804_07682_gb300 import _native as N
+    channel = ("mu", "e", False)
+    edges = np.linspace(500.0, 5000.0, 31)
+    theta, counts, Nn, data, eta, refs = general_case(channel, edges, 16, np.array([810.0]), 3, 1e-3, 1, 51,
+                                                      nuisances=True)
+    plan = api.Plan(edges, [810.0], nodes_per_bin=16, npts=3, norm=Nn, e_scale=1e-3, prec="ff", kind="poisson",
+                    channel=channel)
+    plan.set_graph(graph)
+    d_out = plan.eval_general(plan.params_tensor(theta), dev(data), dev(eta), 0.02, grad=True)
+    torch.cuda.synchronize()
+    c, g = plan.eval_host(theta, data, eta, 0.02, grad=True)
+    assert np.array_equal(c, d_out["chi2"].cpu().numpy()) and np.array_equal(g, d_out["grad"].cpu().numpy())
+    th1 = theta * np.array([1.01, 0.99, 1.02, 0.98, 1.0, 1.01])
+    for _ in range(2):
+        t0 = plan.eval_host_async(theta, data, eta, 0.02)
+        t1 = plan.eval_host_async(th1, data, eta, 0.02)
+        c0, g0 = plan.eval_host_wait(t0)
+        c1, g1 = plan.eval_host_wait(t1)
+        assert np.array_equal(c0, c) and np.array_equal(g0, g)
+    for p in range(3):
+        check_chi2(c[p], refs[p], data, 1, 1e-6, tag="general host p%d" % p)
+        assert normrel(g[p], refs[p]["grad"][:6]) < 1e-4
+        r1 = oracle.chain_general(edges, 16, [810.0], th1[p], Nn, data, "mu", "e", False, 1, eta, 0.02, e_scale=1e-3)
+        check_chi2(c1[p], r1, data, 1, 1e-6, tag="general host th1 p%d" % p)
+    code = N.lib().gna_chain_eval_host(plan._h, ctypes.c_void_p(theta.ctypes.data), None, 0.0,
+                                       ctypes.c_void_p(data.ctypes.data), 0, ctypes.c_void_p(c.ctypes.data), None, None,
+                                       None)
+    assert code == N.GNA_ESTATE
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_general_fits_match_oracle(api, prec):
+    # batched Levenberg-Marquardt fits in all six parameters of nu_mu -> nu_e
+    # appearance at 810 km (40 bins x 12 nodes, 0.5-5 GeV): 6 Poisson
+    # pseudo-data sets from the oracle's prediction at GEN_TH, starts
+    # perturbed by up to 3 %; each fitted again by the oracle's fit_lm
+    edges = np.linspace(500.0, 5000.0, 41)
+    n, k = 12, 6
+    mu_rb, _ = oracle.binned_general(edges, n, [810.0], GEN_TH, "mu", "e", False, 1e-3)
+    Nn = 2e4 / mu_rb[0].sum()
+    data = np.stack([wl.poisson_data(Nn * mu_rb[0], 70 + j) for j in range(k)])
+    start = np.tile(GEN_TH, (k, 1)) * np.random.default_rng(61).uniform(0.97, 1.03, size=(k, 6))
+    plan = api.Plan(edges, [810.0], nodes_per_bin=n, npts=k, norm=Nn, e_scale=1e-3, prec=prec, kind="poisson",
+                    max_datasets=k, channel=("mu", "e", False))
+    params = plan.params_tensor(start).clone()
+    params, chi2 = plan.fit(params, dev(data), iters=20, graph=(prec == "ff"))
+    torch.cuda.synchronize()
+    plan.status()
+    P, C = params.cpu().numpy(), chi2.cpu().numpy()
+    start_chi2 = [oracle.chain_general(edges, n, [810.0], start[j], Nn, data[j], "mu", "e", False, 1,
+                                       e_scale=1e-3)["chi2"] for j in range(k)]
+    for j in range(k):
+        ev = lambda t, j=j: oracle.chain_general(edges, n, [810.0], t, Nn, data[j], "mu", "e", False, 1, e_scale=1e-3)
+        th, c2, _ = oracle.fit_lm(ev, start[j], iters=20)
+        log_err("general fit %s" % prec, chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th))
+        assert C[j] <= start_chi2[j] * (1 + 1e-12)
+        assert rel(C[j], c2) < (1e-9 if prec == "fp64" else 1e-6), (j, C[j], c2)
+        assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
+    plan.close()

@@ -157,6 +157,7 @@ FIT_MUTATIONS = {
     "damping_identity": ("lam * np.diag(np.diag(H))", "lam * np.eye(4)"),
     "gradient_sign": ("np.linalg.solve(A, -g)", "np.linalg.solve(A, g)"),
     "hessian_not_weighted": ('(Jm.T * (2.0 / r["mu"])) @ Jm', "2.0 * Jm.T @ Jm"),
+    "gradient_first_four_only": ('r["grad"][:npar]', 'r["grad"][:4]'),
 }
 
 
@@ -176,3 +177,27 @@ def test_fit_pins_catch_planted_mistake(mut, monkeypatch):
         except (AssertionError, ValueError, FloatingPointError, np.linalg.LinAlgError):
             caught.append(pin.__name__)
     assert caught, "no fitter pin failed for mutation %s" % mut
+
+
+def test_fit_lm_six_parameters_box_and_free_phase():
+    # six parameters in the any-channel order (s2_12, s2_13, s2_23, delta_cp,
+    # dm2_21, dm2_32), diagonal linear problem: the default box clamps s2_23
+    # (target 1.4 > 1 - 1e-6) and leaves delta_cp free (target -2.5); the
+    # others follow the lambda schedule of the four-parameter pin
+    a = np.array([1.0, 2.0, 1.0, 1.0, 0.5, 4.0])
+    v = np.array([1.0, 4.0, 1.0, 2.0, 0.25, 2.0])
+    d = np.array([0.5, 0.3, 1.4, -2.5, 0.7, 2.0])
+    th0 = np.array([0.1, 0.05, 0.5, 1.0, 0.2, 0.1])
+    th, c2, hist = oracle.fit_lm(linear_problem(d, a, v), th0, iters=4, lam0=1.0)
+    assert th[2] == 1.0 - 1e-6
+    free = [0, 1, 3, 4, 5]
+    r = d - a * th0
+    for lam in (0.1, 0.01, 0.001):
+        r = r * lam / (1.0 + lam)
+    assert np.allclose(th[free], ((d - r) / a)[free], rtol=1e-12, atol=1e-15)
+    assert th[3] < 0.0  # delta_cp crossed zero
+    r2 = (d[2] - a[2] * (1.0 - 1e-6)) ** 2 / v[2]
+    assert np.isclose(c2, r2 + np.sum(r[free] ** 2 / v[free]), rtol=1e-9, atol=0.0)
+
+
+FIT_PINS.append(test_fit_lm_six_parameters_box_and_free_phase)

@@ -476,3 +476,29 @@ def test_general_chain_reduces_to_the_ee_chain_and_matches_differences():
     f = lambda t: oracle.chain_general(e2, 10, [810.0], t, N2, d2, "mu", "e", kind=1, e_scale=1e-3)["chi2"]
     gr = oracle.chain_general(e2, 10, [810.0], th, N2, d2, "mu", "e", kind=1, e_scale=1e-3)["grad"][:6]
     assert np.linalg.norm(gr - fd6(f, th)) <= 1e-5 * np.linalg.norm(gr)
+
+
+def test_general_chain_jacobian_matches_central_differences():
+    # J[i][q] = d mu_i / d p_q of the any-channel chain (the fits' Jacobian)
+    # against central differences of mu itself, and the gradient identity
+    # d chi2 / d p = sum_i (d chi2 / d mu_i) J_i for Poisson and Pearson
+    edges = np.linspace(600.0, 4000.0, 9)
+    th = np.array(TH6) * np.array([1.02, 0.97, 1.01, 0.95, 1.03, 0.99])
+    data = np.array([31.0, 57.0, 60.0, 44.0, 38.0, 20.0, 14.0, 9.0])
+    eta = np.random.default_rng(3).normal(0.0, 0.02, 8)
+    for kind in (0, 1):
+        r = oracle.chain_general(edges, 12, [810.0], th, 2e3, data, "mu", "e", False, kind, eta, 0.02, e_scale=1e-3)
+        for q in range(6):
+            h = 1e-6 * abs(th[q])
+            tp, tm = th.copy(), th.copy()
+            tp[q] += h
+            tm[q] -= h
+            mp = oracle.chain_general(edges, 12, [810.0], tp, 2e3, data, "mu", "e", False, kind, eta, 0.02,
+                                      e_scale=1e-3)["mu"]
+            mm = oracle.chain_general(edges, 12, [810.0], tm, 2e3, data, "mu", "e", False, kind, eta, 0.02,
+                                      e_scale=1e-3)["mu"]
+            fd = (mp - mm) / (2 * h)
+            assert np.allclose(r["J"][:, q], fd, rtol=1e-6, atol=1e-9 * np.abs(fd).max()), q
+        mu = r["mu"]
+        g_mu = (1 - data ** 2 / mu ** 2) if kind == 0 else 2 * (1 - data / mu)
+        assert np.allclose(g_mu @ r["J"], r["grad"][:6], rtol=1e-12, atol=0.0)

@@ -36,15 +36,16 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
-def fp32_ops_general(nL: int, grad: bool) -> int:
+def fp32_ops_general(nL: int, grad: bool, surv: bool) -> int:
     """Algorithmic FP32 operations per energy node of the any-channel node
-    kernel: per (node, baseline) the two phases reduced modulo pi/2 (11 each),
-    their sin/cos 10 each and quadrant swaps 3 each (48), angle addition 4,
-    sin^2, sin cos and cos^2 of three phases 9, their weighted sums 9 (18 with
-    hi + lo weights for several baselines), with the gradient cos^2 - sin^2 3
-    and two more weighted sums per phase 6; per node the Kahan product-sums of
-    9 (15) values, 4 each."""
-    per_r = 70 + (9 if nL > 1 else 0) + (9 if grad else 0)
+    kernel: per (node, baseline) the phases reduced modulo pi and their
+    sin/cos 38, angle addition 4, sin^2, sin cos and cos^2 of three phases 9,
+    their weighted sums 9 (18 with hi + lo weights for several baselines),
+    with the gradient cos^2 - sin^2 3 and two more weighted sums per phase 6;
+    per node the Kahan product-sums of 9 (15) values, 4 each.  Survival
+    channels (alpha = beta) reduce the phases modulo pi/2 instead (11 each)
+    with quadrant swaps (3 each): 10 more per (node, baseline)."""
+    per_r = 60 + (9 if nL > 1 else 0) + (9 if grad else 0) + (10 if surv else 0)
     return nL * per_r + (60 if grad else 36)
 
 
@@ -75,8 +76,8 @@ PROFILE_EVERY = 8
 TRAFFIC_CAPTURE = {
     "split": {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
               "bytes": 265113600 + 4114176},
-    "slices": {"sources_sha256": "a7159a9d2817b6941ab11b6b92e3fecc30531eb81a15b5d62a927d4c92bf7dda",
-               "bytes": 268655360 + 5216768 + 8175872},
+    "slices": {"sources_sha256": "9c3abf812af42a03c55e854adc82595478aa674b711dbaaed215612af682df66",
+               "bytes": 268506624 + 4631296 + 8176896 + 2048},
 }
 KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
                   "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h",
@@ -356,7 +357,7 @@ def side_workloads(api, torch, device, args):
     a1.record(stream)
     torch.cuda.synchronize()
     ms = a0.elapsed_time(a1) / reps
-    ops = sum(fp32_ops_general(1, True) * w.nbins * int(n) for n in w.node_counts)
+    ops = sum(fp32_ops_general(1, True, False) * w.nbins * int(n) for n in w.node_counts)  # appearance
     check["scan_numu_nue"] = (w, Ng, datag.cpu().numpy(), og["chi2"].cpu().numpy(), og["grad"].cpu().numpy(), th6)
     out["scan_64x64_500bins_numu_nue"] = {
         "scans_per_s": 1e3 / ms, "ms_per_scan": ms, "chi2_grad_evals_per_s": w.npts * 1e3 / ms,

@@ -155,46 +155,53 @@ cudaError_t launch_prepare_general(const gna_osc_full* prm, int npts, const Base
 }
 
 // ------------------------------------------------------------ launchers ----
-template <int PH, int NL, bool GRAD>
+template <int PH, int NL, bool GRAD, bool SURV>
 static cudaError_t launch_gen(const GenArgs& a, int grid, int block, cudaStream_t s) {
-    return launch_dependent(k_fused_bins_gen<PH, NL, GRAD>, a, grid, block, s);
+    return launch_dependent(k_fused_bins_gen<PH, NL, GRAD, SURV>, a, grid, block, s);
+}
+
+template <int PH, int NL>
+static cudaError_t launch_gen_nl(bool grad, bool surv, const GenArgs& a, int grid, int block, cudaStream_t s) {
+    if (grad) return surv ? launch_gen<PH, NL, true, true>(a, grid, block, s) : launch_gen<PH, NL, true, false>(a, grid, block, s);
+    return surv ? launch_gen<PH, NL, false, true>(a, grid, block, s) : launch_gen<PH, NL, false, false>(a, grid, block, s);
 }
 
 template <int PH>
-static cudaError_t dispatch_gen_ph(int nl, bool grad, const GenArgs& a, int grid, int block, cudaStream_t s) {
-    switch (nl * 2 + (grad ? 1 : 0)) {
-        case 2: return launch_gen<PH, 1, false>(a, grid, block, s);
-        case 3: return launch_gen<PH, 1, true>(a, grid, block, s);
-        case 4: return launch_gen<PH, 2, false>(a, grid, block, s);
-        case 5: return launch_gen<PH, 2, true>(a, grid, block, s);
-        case 8: return launch_gen<PH, 4, false>(a, grid, block, s);
-        case 9: return launch_gen<PH, 4, true>(a, grid, block, s);
-        case 16: return launch_gen<PH, 8, false>(a, grid, block, s);
-        case 17: return launch_gen<PH, 8, true>(a, grid, block, s);
+static cudaError_t dispatch_gen_ph(int nl, bool grad, bool surv, const GenArgs& a, int grid, int block, cudaStream_t s) {
+    switch (nl) {
+        case 1: return launch_gen_nl<PH, 1>(grad, surv, a, grid, block, s);
+        case 2: return launch_gen_nl<PH, 2>(grad, surv, a, grid, block, s);
+        case 4: return launch_gen_nl<PH, 4>(grad, surv, a, grid, block, s);
+        case 8: return launch_gen_nl<PH, 8>(grad, surv, a, grid, block, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int PH>
-static int resident_gen_ph(int nl, bool grad, int block) {
+template <typename Kernel>
+static int occupancy(Kernel k, int block) {
     int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (nl * 2 + (grad ? 1 : 0)) {
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 1, false>, block, 0); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 1, true>, block, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 2, false>, block, 0); break;
-        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 2, true>, block, 0); break;
-        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 4, false>, block, 0); break;
-        case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 4, true>, block, 0); break;
-        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 8, false>, block, 0); break;
-        case 17: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_bins_gen<PH, 8, true>, block, 0); break;
-        default: break;
-    }
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     return n > 0 ? n : 1;
+}
+
+template <int PH, int NL>
+static int resident_gen_nl(bool grad, bool surv, int block) {
+    if (grad) return surv ? occupancy(k_fused_bins_gen<PH, NL, true, true>, block) : occupancy(k_fused_bins_gen<PH, NL, true, false>, block);
+    return surv ? occupancy(k_fused_bins_gen<PH, NL, false, true>, block) : occupancy(k_fused_bins_gen<PH, NL, false, false>, block);
+}
+
+template <int PH>
+static int resident_gen_ph(int nl, bool grad, bool surv, int block) {
+    switch (nl) {
+        case 1: return resident_gen_nl<PH, 1>(grad, surv, block);
+        case 2: return resident_gen_nl<PH, 2>(grad, surv, block);
+        case 4: return resident_gen_nl<PH, 4>(grad, surv, block);
+        case 8: return resident_gen_nl<PH, 8>(grad, surv, block);
+        default: return 1;
+    }
 }
 
 static int resident_gen64(int nl, bool grad, int block) {
@@ -218,9 +225,9 @@ static int resident_gen64(int nl, bool grad, int block) {
     return n > 0 ? n : 1;
 }
 
-int general_resident_ctas(int ph, int nl, bool grad, int block) {
+int general_resident_ctas(int ph, int nl, bool grad, bool surv, int block) {
     if (ph == 2) return resident_gen64(nl, grad, block);
-    return ph == 0 ? resident_gen_ph<0>(nl, grad, block) : resident_gen_ph<1>(nl, grad, block);
+    return ph == 0 ? resident_gen_ph<0>(nl, grad, surv, block) : resident_gen_ph<1>(nl, grad, surv, block);
 }
 
 template <int NL, bool GRAD>
@@ -243,9 +250,10 @@ cudaError_t dispatch_general64(int nl, bool grad, const GenArgs64& a, int grid, 
     }
 }
 
-cudaError_t dispatch_general(int ph, int nl, bool grad, const GenArgs& a, int grid, int block, cudaStream_t s) {
-    if (ph == 0) return dispatch_gen_ph<0>(nl, grad, a, grid, block, s);
-    if (ph == 1) return dispatch_gen_ph<1>(nl, grad, a, grid, block, s);
+cudaError_t dispatch_general(int ph, int nl, bool grad, bool surv, const GenArgs& a, int grid, int block,
+                             cudaStream_t s) {
+    if (ph == 0) return dispatch_gen_ph<0>(nl, grad, surv, a, grid, block, s);
+    if (ph == 1) return dispatch_gen_ph<1>(nl, grad, surv, a, grid, block, s);
     return cudaErrorInvalidValue;
 }
 

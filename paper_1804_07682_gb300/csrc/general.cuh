@@ -22,12 +22,14 @@
 // Survival channels cancel: P = 1 + sum a S with a = -4 |V_ai|^2 |V_aj|^2 of
 // order -1, so where S -> 1 (a disappearance dip) M is a small difference of
 // sum W and a U, and the FP32 rounding of S near 1 (~6e-8 absolute per node)
-// becomes a large relative error of M.  The mixed node pass therefore also
-// accumulates Q_ij = sum_k W_k sum_r omega_r cos^2 x_ij, and the epilogue takes
-// each pair's sine sum either as U_ij or, when Q_ij < U_ij, as
+// becomes a large relative error of M.  Appearance channels cancel too, less:
+// by unitarity a_31 S_31 + a_32 S_32 (terms of ~0.2 for nu_mu -> nu_e) nearly
+// cancel as both S -> 1.  The mixed node pass therefore also accumulates
+// Q_ij = sum_k W_k sum_r omega_r cos^2 x_ij, and the epilogue takes each
+// pair's sine sum either as U_ij or, when Q_ij < U_ij, as
 // sum_k W_k sum_r omega_r - Q_ij (sin^2 + cos^2 = 1, applied in double): both
 // sums add positive terms, so the one used carries an error relative to the
-// smaller of the two, which is small wherever P dips.
+// smaller of the two, and the large parts cancel in double.
 // These kernels reuse the energy-grid layouts, the bin/slice task scheme and
 // the group and point reductions of the nue_bar survival chain; they are
 // separate kernels so that the survival chain's code stays as it is.
@@ -109,7 +111,12 @@ __device__ __forceinline__ void sincos_quadrant(float r, bool odd, float& s, flo
     c = odd ? -sr : cr;
 }
 
-template <int PH, int NL, bool GRAD>
+// SURV: a survival channel (delta_ab = 1), whose P goes to ~0 at a
+// disappearance minimum: the phases are then reduced modulo pi/2 with
+// quadrant swaps, so that cos x near its zeros (the cos^2 sums there) keeps
+// its relative accuracy; other channels reduce modulo pi (P stays well above
+// the cos^2 errors there).
+template <int PH, int NL, bool GRAD, bool SURV>
 struct NodeMathGen {
     static constexpr int NV = gen_nv(GRAD);
     // with several baselines the weights enter as hi + lo (no bias from the
@@ -139,17 +146,30 @@ struct NodeMathGen {
 #pragma unroll
         for (int r = 0; r < NL; r++) {
             float s1, c1, s2, c2;
-            float r21, r32;
-            bool o21, o32;
-            if (PH == 0) {
-                r21 = reduce_pi2_ff(ph.ch21[r], ph.cl21[r], eh, el, o21);
-                r32 = reduce_pi2_ff(ph.ch32[r], ph.cl32[r], eh, el, o32);
+            if constexpr (SURV) {
+                bool o21, o32;
+                float r21, r32;
+                if (PH == 0) {
+                    r21 = reduce_pi2_ff(ph.ch21[r], ph.cl21[r], eh, el, o21);
+                    r32 = reduce_pi2_ff(ph.ch32[r], ph.cl32[r], eh, el, o32);
+                } else {
+                    r21 = reduce_pi2_f64(ph.cd21[r], ed, o21);
+                    r32 = reduce_pi2_f64(ph.cd32[r], ed, o32);
+                }
+                sincos_quadrant(r21, o21, s1, c1);
+                sincos_quadrant(r32, o32, s2, c2);
             } else {
-                r21 = reduce_pi2_f64(ph.cd21[r], ed, o21);
-                r32 = reduce_pi2_f64(ph.cd32[r], ed, o32);
+                float r21, r32;
+                if (PH == 0) {
+                    r21 = reduce_pi_ff(ph.ch21[r], ph.cl21[r], eh, el);
+                    r32 = reduce_pi_ff(ph.ch32[r], ph.cl32[r], eh, el);
+                } else {
+                    r21 = reduce_pi_f64(ph.cd21[r], ed);
+                    r32 = reduce_pi_f64(ph.cd32[r], ed);
+                }
+                sincos_poly(r21, s1, c1);
+                sincos_poly(r32, s2, c2);
             }
-            sincos_quadrant(r21, o21, s1, c1);
-            sincos_quadrant(r32, o32, s2, c2);
             // x31 = x21 + x32 up to a multiple of pi: sin^2, sin cos and
             // cos^2 - sin^2 do not see it
             const float s3 = fmaf(s1, c2, c1 * s2);
@@ -189,8 +209,8 @@ struct NodeMathGen {
 
 // Bin i of point p from its summed values [U(3), V(3)] (+ [Y(3), Z(3)]) and
 // Q(3): vd = {U, V, Q} (nine values) in double, vf the NV values in FP32, and
-// the point's coefficients.  Each pair's sine sum is U, or sum W sum omega - Q
-// where Q is the smaller sum (see the header); M is formed in double (its
+// the point's coefficients.  Each pair's sine sum is U, or sum W sum omega - Q where Q is
+// the smaller sum (see the header); M is formed in double (its
 // terms may cancel), its six derivatives in FP32, then the chi^2 term and its
 // gradient contributions into regs[0..6] (float pairs): [0] the chi^2 term,
 // [1 + q] g_i N (1 + eta_i) dM/dp_q.
@@ -308,9 +328,9 @@ static __device__ __noinline__ void gen_group_done(const EpiArgs& a, int p, int 
 
 // Node kernel of the general channel, bin and slice mappings: the task scheme
 // and node loop of k_fused_bins with the channel-free sums above.
-template <int PH, int NL, bool GRAD>
+template <int PH, int NL, bool GRAD, bool SURV>
 __global__ void __launch_bounds__(256) k_fused_bins_gen(GenArgs ga) {
-    using M = NodeMathGen<PH, NL, GRAD>;
+    using M = NodeMathGen<PH, NL, GRAD, SURV>;
     constexpr int NV = M::NV;
     const BinArgs& a = ga.b;
     const int lane = threadIdx.x & 31;
@@ -586,8 +606,9 @@ __global__ void __launch_bounds__(256) k_fused64_bins_gen(GenArgs64 ga) {
 cudaError_t launch_prepare_general(const gna_osc_full* prm, int npts, const BaseConst& bc, int alpha, int beta,
                                    int anti, PointConst* out, GenConst* gout, int* zero, int64_t nz, int* status,
                                    cudaStream_t s);
-cudaError_t dispatch_general(int ph, int nl, bool grad, const GenArgs& a, int grid, int block, cudaStream_t s);
-int general_resident_ctas(int ph, int nl, bool grad, int block);
+cudaError_t dispatch_general(int ph, int nl, bool grad, bool surv, const GenArgs& a, int grid, int block,
+                             cudaStream_t s);
+int general_resident_ctas(int ph, int nl, bool grad, bool surv, int block);
 cudaError_t dispatch_general64(int nl, bool grad, const GenArgs64& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_slices_reduce_general(const float2* part, int S, int NV, const EpiArgs& ea, const GenConst* gc,
                                          int npts, cudaStream_t s);

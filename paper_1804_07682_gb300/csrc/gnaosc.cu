@@ -466,6 +466,7 @@ gna_status enqueue_eval(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* l
 // q.H set for the fits' J^T W J); counts kernel launches into *launches.
 gna_status enqueue_eval_general(gna_plan* plan, const EvalReq& q, cudaStream_t s, int* launches) {
     const bool grad = q.grad || q.grad_eta || q.H;
+    const bool surv = plan->g_alpha == plan->g_beta;  // survival channel: phases modulo pi/2 (general.cuh)
     const int NV = gen_nv(grad);
     SliceShape ssh{1, 0, plan->ntasks};
     if (plan->mapping == MAP_SLICES) {
@@ -479,7 +480,7 @@ gna_status enqueue_eval_general(gna_plan* plan, const EvalReq& q, cudaStream_t s
     ea.NBV = q.H ? kGenNBVFit : (grad ? 7 : 1);  // chi2, the six-parameter gradient terms, J^T W J
     ea.binsums = nullptr;
     const bool sliced = ssh.S > 1;
-    int64_t g = (int64_t)plan->sm_count * general_resident_ctas(plan->ph, plan->nl_inst, grad, plan->block);
+    int64_t g = (int64_t)plan->sm_count * general_resident_ctas(plan->ph, plan->nl_inst, grad, surv, plan->block);
     g = std::max<int64_t>(1, std::min<int64_t>(g, ((int64_t)ssh.ntasks * 32 + plan->block - 1) / plan->block));
     if (plan->ph == 2) {
         GenArgs64 ga64{BinArgs64{plan->grid64_bins, plan->d_goff, plan->d_gn, plan->d_gid, plan->d_tasks, plan->ntasks,
@@ -493,7 +494,7 @@ gna_status enqueue_eval_general(gna_plan* plan, const EvalReq& q, cudaStream_t s
                        plan->ngroups, plan->nbins, plan->d_pc, plan->bc, plan->d_counters, ea, ssh.S, ssh.L,
                        sliced ? plan->d_slices : nullptr},
                plan->d_gc};
-    CU(dispatch_general(plan->ph, plan->nl_inst, grad, ga, (int)g, plan->block, s));
+    CU(dispatch_general(plan->ph, plan->nl_inst, grad, surv, ga, (int)g, plan->block, s));
     *launches = 2;
     if (sliced) {
         CU(launch_slices_reduce_general(plan->d_slices, ssh.S, NV, ea, plan->d_gc, plan->npts, s));

@@ -603,6 +603,7 @@ def test_fits_match_oracle(api, prec):
     for j in range(w.npts):
         ev = lambda t, j=j: oracle.chain(w.edges, w.nodes_per_bin, w.L, t, case.N, case.data[j], w.kind)
         th, c2, _ = oracle.fit_lm(ev, w.theta[j], iters=20)
+        log_err("fit %s" % prec, chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th))
         assert rel(C[j], c2) < (1e-9 if prec == "fp64" else 1e-6), (j, C[j], c2)
         assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
 

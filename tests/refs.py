@@ -46,6 +46,15 @@ def rel(a, b):
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
 
 
+def fit_sigma(r):
+    """Statistical errors of the fitted parameters at an oracle evaluation r:
+    the square roots of the diagonal of the inverse expected Fisher matrix
+    sum_i (2 / mu_i) J_i J_i^T (the matrix the fitter's steps are built on)."""
+    J = np.asarray(r["J"], dtype=np.float64)
+    H = (J.T * (2.0 / np.asarray(r["mu"], dtype=np.float64))) @ J
+    return np.sqrt(np.diag(np.linalg.inv(H)))
+
+
 def normrel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)

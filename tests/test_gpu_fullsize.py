@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_1804_07682_gb300 import workloads as wl
-from refs import Case, check_chi2, log_err, normrel, rel
+from refs import Case, check_chi2, fit_sigma, log_err, normrel, rel
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
@@ -113,9 +113,13 @@ def test_fits_full_sampled(api):
     for j in [0, 9999]:
         ev = lambda t, j=j: oracle.chain(w.edges, w.nodes_per_bin, w.L, t, case.N, case.data[j], w.kind)
         th, c2, _ = oracle.fit_lm(ev, w.theta[j], iters=20)
-        log_err("fit full ff", chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th))
+        pull = float(np.max(np.abs(P[j] - th) / fit_sigma(ev(th))))
+        log_err("fit full ff", chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th), pull=pull)
         assert rel(C[j], c2) < 1e-6, (j, C[j], c2)
-        assert rel(P[j], th) < 1e-3, (j, P[j], th)
+        # largest measured 3.8e-6 relative (the benchmark's worst over 256
+        # data sets against the all-double fits: 1.0e-4)
+        assert rel(P[j], th) < 1e-4, (j, P[j], th)
+        assert pull < 1e-2, (j, pull)
 
 
 def test_pseudo_data_full_size_sampled(api):

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 import oracle
 from paper_1804_07682_gb300 import _native as N
 from paper_1804_07682_gb300 import workloads as wl
-from refs import Case, check_chi2, log_err, normrel, rel
+from refs import Case, check_chi2, fit_sigma, log_err, normrel, rel
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
@@ -603,9 +603,14 @@ def test_fits_match_oracle(api, prec):
     for j in range(w.npts):
         ev = lambda t, j=j: oracle.chain(w.edges, w.nodes_per_bin, w.L, t, case.N, case.data[j], w.kind)
         th, c2, _ = oracle.fit_lm(ev, w.theta[j], iters=20)
-        log_err("fit %s" % prec, chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th))
+        pull = float(np.max(np.abs(P[j] - th) / fit_sigma(ev(th))))
+        log_err("fit %s" % prec, chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th), pull=pull)
         assert rel(C[j], c2) < (1e-9 if prec == "fp64" else 1e-6), (j, C[j], c2)
-        assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
+        # mixed: largest measured 7.7e-6 relative
+        assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-4), (j, P[j], th)
+        # in units of the parameters' statistical errors the two fits agree far
+        # inside any physics resolution
+        assert pull < (1e-5 if prec == "fp64" else 1e-2), (j, pull)
 
 
 def test_pseudo_data_matches_oracle_bit_for_bit(api):
@@ -888,5 +893,9 @@ def test_general_fits_match_oracle(api, prec):
         log_err("general fit %s" % prec, chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th))
         assert C[j] <= start_chi2[j] * (1 + 1e-12)
         assert rel(C[j], c2) < (1e-9 if prec == "fp64" else 1e-6), (j, C[j], c2)
+        # mixed: up to 5.4e-4 relative measured.  One appearance channel does
+        # not determine six parameters (the Fisher matrix's condition number
+        # is ~3e17 at the generating point), so the fits wander along flat
+        # directions and no statistical errors exist to measure them in
         assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-3), (j, P[j], th)
     plan.close()

@@ -201,3 +201,14 @@ def test_fit_lm_six_parameters_box_and_free_phase():
 
 
 FIT_PINS.append(test_fit_lm_six_parameters_box_and_free_phase)
+
+
+def test_fit_sigma_is_the_inverse_fisher_diagonal():
+    # the parity tests' statistical errors: J = [[1, 0], [0, 2], [1, 1]] and
+    # mu = 2 give H = J^T J = [[2, 1], [1, 5]], H^-1 = [[5, -1], [-1, 2]] / 9
+    import refs
+    r = {"J": np.array([[1.0, 0.0], [0.0, 2.0], [1.0, 1.0]]), "mu": np.full(3, 2.0)}
+    assert np.allclose(refs.fit_sigma(r), [np.sqrt(5.0 / 9.0), np.sqrt(2.0 / 9.0)], rtol=1e-14, atol=0.0)
+    # halving every mu doubles H: the errors shrink by sqrt(2)
+    r["mu"] = np.full(3, 1.0)
+    assert np.allclose(refs.fit_sigma(r), [np.sqrt(5.0 / 18.0), np.sqrt(1.0 / 9.0)], rtol=1e-14, atol=0.0)

@@ -463,6 +463,16 @@ gna_status gna_plan_profile_read(gna_plan* plan, double* total_ms, int* launches
  * GNA_EINVAL for out == NULL, blocks < 1 or iters < 1. */
 gna_status gna_fp32_probe(int blocks, int iters, float* out, void* stream);
 
+/* gna_grad_scale: the chain rule's last step for a caller that differentiates
+ * a function of chi^2 (an autograd engine): with s = d loss / d chi^2 on the
+ * device, a[i] *= *s for i < na and b[j] *= *s for j < nb, in place, in one
+ * launch on `stream` (a = d chi2 / d theta, b = d chi2 / d eta as an
+ * evaluation wrote them).  a, b, s: device memory of the current device,
+ * float64, owned by the caller; a (b) may be NULL when na (nb) is 0.
+ * GNA_EINVAL for s == NULL, negative counts or a NULL array with a positive
+ * count; GNA_ECUDA if the launch fails. */
+gna_status gna_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s, void* stream);
+
 
 /* ---------------------------------------------------------------------------
  * gna_chain_eval_noalloc: chi^2 (and optionally its gradient and the binned

@@ -100,6 +100,7 @@ SIGNATURES = {
     "gna_plan_profile": (c_int, [c_void_p, c_int]),
     "gna_plan_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "gna_fp32_probe": (c_int, [c_int, c_int, c_void_p, c_void_p]),
+    "gna_grad_scale": (c_int, [c_void_p, ctypes.c_int64, c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
     "gna_chain_eval_general_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_void_p, c_void_p,
                                             c_void_p]),
     "gna_chain_eval_general_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_int, c_int,

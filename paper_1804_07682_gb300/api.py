@@ -593,8 +593,9 @@ class OscChi2(torch.autograd.Function):
 
     theta has 4 parameters on a survival-chain plan and 6 on an any-channel
     plan.  forward runs one fused evaluation with the tangents on and keeps
-    d chi2 / d theta (and d chi2 / d eta); backward returns grad_output times
-    the kept gradient.
+    d chi2 / d theta (and d chi2 / d eta); backward scales the kept gradient
+    by grad_output in place (one launch) and returns it, so one chi2 can be
+    differentiated once (a second backward through it raises RuntimeError).
     """
 
     @staticmethod
@@ -608,14 +609,26 @@ class OscChi2(torch.autograd.Function):
         ctx.g_theta = torch.empty(theta.shape, dtype=torch.float64, device=theta.device)
         ctx.g_eta = None if eta is None else torch.empty(eta.shape, dtype=torch.float64, device=theta.device)
         plan._eval_into(theta, data, eta, sigma, chi2, ctx.g_theta, ctx.g_eta)
+        ctx.lib = plan._lib
         return chi2
 
     @staticmethod
     def backward(ctx, go):
-        # fresh (non-view) tensors, which the gradient accumulation takes as
-        # they are instead of copying
-        ge = torch.mul(ctx.g_eta, go) if ctx.g_eta is not None else None
-        return torch.mul(ctx.g_theta, go), ge, None, None, None
+        # the kept gradient is scaled by grad_output in place, one launch for
+        # theta and eta (gna_grad_scale), and handed to the gradient
+        # accumulation, which takes fresh non-view tensors as they are; so
+        # it can be handed out once
+        if ctx.g_theta is None:
+            raise RuntimeError("OscChi2: a second backward through the same chi2 needs a new evaluation")
+        gt, ge = ctx.g_theta, ctx.g_eta
+        ctx.g_theta = ctx.g_eta = None
+        if not (go.is_cuda and go.dtype == torch.float64 and go.device == gt.device and go.numel() == 1):
+            raise ValueError("OscChi2: grad_output must be a float64 scalar on the evaluation's device")
+        code = ctx.lib.gna_grad_scale(gt.data_ptr(), gt.numel(), None if ge is None else ge.data_ptr(),
+                                      0 if ge is None else ge.numel(), go.data_ptr(),
+                                      torch.cuda.current_stream(gt.device).cuda_stream)
+        N.check(code, what="gna_grad_scale")
+        return gt, ge, None, None, None
 
 
 def chi2(theta, plan: Plan, data, eta=None, sigma: float = 0.0):

@@ -1715,6 +1715,12 @@ gna_status gna_fp32_probe(int blocks, int iters, float* out, void* stream) {
     return launch_fma_probe(blocks, iters, out, (cudaStream_t)stream) == cudaSuccess ? GNA_OK : GNA_ECUDA;
 }
 
+gna_status gna_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s, void* stream) {
+    if (!s || na < 0 || nb < 0 || (na > 0 && !a) || (nb > 0 && !b) || na > INT64_MAX / 2 || nb > INT64_MAX / 2)
+        return GNA_EINVAL;
+    return launch_grad_scale(a, na, b, nb, s, (cudaStream_t)stream) == cudaSuccess ? GNA_OK : GNA_ECUDA;
+}
+
 gna_status gna_plan_profile(gna_plan* plan, int on) {
     if (!plan) return GNA_EINVAL;
     destroy_profile(plan);

@@ -599,4 +599,22 @@ cudaError_t launch_fma_probe(int blocks, int iters, float* out, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// a[i] *= *s (i < na), b[j] *= *s (j < nb): one grid-stride pass over both.
+__global__ void __launch_bounds__(256) k_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s) {
+    const double f = *s;
+    const int64_t n = na + nb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < na) a[i] *= f;
+        else b[i - na] *= f;
+    }
+}
+
+cudaError_t launch_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s, cudaStream_t st) {
+    const int64_t n = na + nb;
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    k_grad_scale<<<grid, 256, 0, st>>>(a, na, b, nb, s);
+    return cudaGetLastError();
+}
+
 }  // namespace gna

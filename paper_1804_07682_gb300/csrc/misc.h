@@ -96,6 +96,7 @@ template <int NP>
 cudaError_t launch_lm_update(int npts, const double* chi2, const double* grad, const double* H, LMStateT<NP>* st,
                              double* prm, double* chi2_best, cudaStream_t s);
 cudaError_t launch_fma_probe(int blocks, int iters, float* out, cudaStream_t s);
+cudaError_t launch_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s, cudaStream_t st);
 template <int NP>
 cudaError_t launch_lm_finish(int npts, const LMStateT<NP>* st, double* prm, cudaStream_t s);
 

@@ -565,10 +565,19 @@ def test_autograd_function(api):
     theta = dev(w.theta[0]).requires_grad_(True)
     eta = dev(w.eta).requires_grad_(True)
     c = api.chi2(theta, plan, d, eta, w.sigma_eta)
-    (2.0 * c).backward()
+    (2.0 * c).backward(retain_graph=True)
     ref = case.oracle_point(0)
     assert normrel(theta.grad.cpu().numpy(), 2.0 * ref["grad"][:4]) < 1e-9
     assert normrel(eta.grad.cpu().numpy(), 2.0 * ref["grad"][4:]) < 1e-9
+    # the kept gradient was handed out (scaled in place): a second backward
+    # through the same chi2 is refused, the first one's gradients stay
+    with pytest.raises(RuntimeError):
+        c.backward()
+    assert normrel(theta.grad.cpu().numpy(), 2.0 * ref["grad"][:4]) < 1e-9
+    # accumulation over two evaluations
+    api.chi2(theta, plan, d, eta, w.sigma_eta).backward()
+    assert normrel(theta.grad.cpu().numpy(), 3.0 * ref["grad"][:4]) < 1e-9
+    assert normrel(eta.grad.cpu().numpy(), 3.0 * ref["grad"][4:]) < 1e-9
 
     # FP64 central differences (h = 1e-6 relative) through the same plan
     def f(t):

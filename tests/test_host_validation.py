@@ -155,3 +155,16 @@ def test_noalloc_wrapper_refuses_bad_arguments_before_any_launch():
     # every dtype and shape right, but host tensors: refused for the device
     with pytest.raises(ValueError, match="CUDA tensors"):
         api.chi2_noalloc(E, W, [52.5], p, d, 1.0)
+
+
+def test_grad_scale_refuses_bad_arguments(N):
+    L = N.lib()
+    s = ctypes.c_double(2.0)
+    assert L.gna_grad_scale(None, 4, None, 0, None, None) == EINVAL  # no scale factor
+    assert L.gna_grad_scale(None, 4, None, 0, ctypes.addressof(s), None) == EINVAL  # a = NULL, na = 4
+    assert L.gna_grad_scale(None, 0, None, 3, ctypes.addressof(s), None) == EINVAL  # b = NULL, nb = 3
+    buf = (ctypes.c_double * 4)()
+    assert L.gna_grad_scale(ctypes.addressof(buf), -1, None, 0, ctypes.addressof(s), None) == EINVAL
+    assert L.gna_grad_scale(ctypes.addressof(buf), 4, ctypes.addressof(buf), -2, ctypes.addressof(s), None) == EINVAL
+    # nothing to scale: no launch, success
+    assert L.gna_grad_scale(None, 0, None, 0, ctypes.addressof(s), None) == OK

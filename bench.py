@@ -40,12 +40,13 @@ def fp32_ops_general(nL: int, grad: bool, surv: bool) -> int:
     """Algorithmic FP32 operations per energy node of the any-channel node
     kernel: per (node, baseline) the phases reduced modulo pi and their
     sin/cos 38, angle addition 4, sin^2, sin cos and cos^2 of three phases 9,
-    their weighted sums 9 (18 with hi + lo weights for several baselines),
+    their weighted sums over the baselines 9 (18 with hi + lo weights for
+    several baselines; none for one baseline, whose weight is exactly 1),
     with the gradient cos^2 - sin^2 3 and two more weighted sums per phase 6;
     per node the Kahan product-sums of 9 (15) values, 4 each.  Survival
     channels (alpha = beta) reduce the phases modulo pi/2 instead (11 each)
     with quadrant swaps (3 each): 10 more per (node, baseline)."""
-    per_r = 60 + (9 if nL > 1 else 0) + (9 if grad else 0) + (10 if surv else 0)
+    per_r = 51 + (18 if nL > 1 else 0) + (9 if grad else 0) + (10 if surv else 0)
     return nL * per_r + (60 if grad else 36)
 
 
@@ -55,7 +56,8 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     Per (node, baseline): double-float phase and two-part reduction mod pi
     2 x 9, sin/cos polynomials 2 x 10 (u = r^2, degree-9 sine 5, degree-8
     cosine 4), angle addition 2, three squares, three weighted sums
-    (38 + 2 + 3 + 3 = 46);
+    (38 + 2 + 3 + 3 = 46; 43 for one baseline, whose weight is exactly 1
+    and needs no sums);
     with one or more baselines and no per-baseline sums the weights enter as
     hi + lo (3 more); gradient: cos of the sum 2, three sin*cos products and
     three weighted sums (8); spectra: P_r 3 + Kahan product-sum 4 (7).  Per
@@ -64,7 +66,7 @@ def fp32_ops_per_node(nL: int, grad: bool, spec: bool) -> int:
     product-sums 16.
     """
     omlo = nL > 1 and not spec
-    per_r = 46 + (3 if omlo else 0) + (8 if grad else 0) + (7 if spec else 0)
+    per_r = (46 if nL > 1 else 43) + (3 if omlo else 0) + (8 if grad else 0) + (7 if spec else 0)
     per_node = 11 + (3 if omlo else 0) + (26 if grad else 0)
     return nL * per_r + per_node
 

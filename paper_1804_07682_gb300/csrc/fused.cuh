@@ -107,9 +107,16 @@ struct NodeMath {
             // of sin and cos and leaves sin^2 and sin cos unchanged)
             float s3 = fmaf(s1, c2, c1 * s2);
             float S21 = s1 * s1, S31 = s3 * s3, S32 = s2 * s2;
-            U21 = fmaf(om[r], S21, U21);
-            U31 = fmaf(om[r], S31, U31);
-            U32 = fmaf(om[r], S32, U32);
+            if constexpr (NL == 1) {
+                // one baseline: omega = w / w = 1 exactly, so the weighting is the identity
+                U21 = S21;
+                U31 = S31;
+                U32 = S32;
+            } else {
+                U21 = fmaf(om[r], S21, U21);
+                U31 = fmaf(om[r], S31, U31);
+                U32 = fmaf(om[r], S32, U32);
+            }
             if (OMLO) {
                 L21 = fmaf(omlo[r], S21, L21);
                 L31 = fmaf(omlo[r], S31, L31);

@@ -180,9 +180,16 @@ struct NodeMathGen {
             const float Cs[3] = {c1 * c1, c3 * c3, c2 * c2};
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                U[j] = fmaf(om[r], S[j], U[j]);
-                V[j] = fmaf(om[r], C[j], V[j]);
-                Q[j] = fmaf(om[r], Cs[j], Q[j]);
+                if constexpr (NL == 1) {
+                    // one baseline: omega = w / w = 1 exactly, so the weighting is the identity
+                    U[j] = S[j];
+                    V[j] = C[j];
+                    Q[j] = Cs[j];
+                } else {
+                    U[j] = fmaf(om[r], S[j], U[j]);
+                    V[j] = fmaf(om[r], C[j], V[j]);
+                    Q[j] = fmaf(om[r], Cs[j], Q[j]);
+                }
                 if constexpr (LO) {
                     U[j] = fmaf(omlo[r], S[j], U[j]);
                     V[j] = fmaf(omlo[r], C[j], V[j]);

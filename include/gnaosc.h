@@ -84,7 +84,7 @@ typedef struct {
     const int32_t* node_counts; /* host [npts] per-point order (points of equal order share a grid), or NULL */
     int nL;                     /* baselines, 1..16 */
     const double* L;            /* host [nL], km, > 0 */
-    const double* Lweight;      /* host [nL] combination weights, or NULL for 1/L^2 normalised to sum 1 */
+    const double* Lweight;      /* host [nL] combination weights (finite, >= 0, positive finite sum; normalised to sum 1), or NULL for 1/L^2 */
     double norm;                /* N: mu_i = N (1 + eta_i) sum_r omega_r mu_r,i */
     double e_scale;             /* spectrum S(E * e_scale): 1 for MeV, 1e-3 for GeV */
     gna_precision prec;

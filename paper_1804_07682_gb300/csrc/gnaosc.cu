@@ -1135,8 +1135,16 @@ gna_status gna_plan_create(gna_plan** out, const gna_plan_desc* d, void* stream)
     if (d->kind != GNA_PEARSON && d->kind != GNA_POISSON) return GNA_EINVAL;
     for (int i = 0; i < d->nbins; i++)
         if (!(d->edges[i] > 0.0) || !(d->edges[i + 1] > d->edges[i])) return GNA_EINVAL;
-    for (int r = 0; r < d->nL; r++)
-        if (!(d->L[r] > 0.0) || (d->Lweight && !(d->Lweight[r] >= 0.0))) return GNA_EINVAL;
+    double lw_sum = 0.0;
+    for (int r = 0; r < d->nL; r++) {
+        if (!(d->L[r] > 0.0) || !std::isfinite(d->L[r])) return GNA_EINVAL;
+        if (d->Lweight) {
+            if (!(d->Lweight[r] >= 0.0) || !std::isfinite(d->Lweight[r])) return GNA_EINVAL;
+            lw_sum += d->Lweight[r];
+        }
+    }
+    // the weights are normalised by their sum: it must be positive and finite
+    if (d->Lweight && !(lw_sum > 0.0 && std::isfinite(lw_sum))) return GNA_EINVAL;
     for (int p = 0; p < d->npts; p++) {
         const int n = d->node_counts ? d->node_counts[p] : d->nodes_per_bin;
         if (n < 1 || n > GNA_MAX_ORDER) return GNA_ESHAPE;

@@ -9,6 +9,7 @@
 // different host threads on the same device) race on it and give wrong
 // results; serialise them.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -191,11 +192,12 @@ extern "C" gna_status gna_chain_eval_noalloc(int nbins, int n, const double* E, 
     double wsum = 0.0;
     double om[kMaxNL];
     for (int r = 0; r < nL; r++) {
-        if (!(L[r] > 0.0) || (Lweight && !(Lweight[r] >= 0.0))) return GNA_EINVAL;
+        if (!(L[r] > 0.0) || !std::isfinite(L[r]) || (Lweight && !(Lweight[r] >= 0.0 && std::isfinite(Lweight[r]))))
+            return GNA_EINVAL;
         om[r] = Lweight ? Lweight[r] : 1.0 / (L[r] * L[r]);
         wsum += om[r];
     }
-    if (!(wsum > 0.0)) return GNA_EINVAL;
+    if (!(wsum > 0.0) || !std::isfinite(wsum)) return GNA_EINVAL;
     double fall = 0.0;
     for (int r = 0; r < nL; r++) {
         om[r] /= wsum;

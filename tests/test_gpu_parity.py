@@ -557,6 +557,23 @@ def test_mapping_is_a_tuning_choice_on_small_grids(api, prec):
     forced.close()
 
 
+def test_grad_scale_scales_both_arrays_in_place(api):
+    # the autograd backward's chain-rule step: a *= s, b *= s in one launch,
+    # including a grid-stride pass (more elements than 1024 blocks x 256)
+    from paper_1804_07682_gb300 import _native as N
+    lib = N.lib()
+    s = torch.tensor(-2.5, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for na, nb in ((4, 0), (0, 7), (4, 1000), (300001, 262145)):
+        a = torch.arange(na, dtype=torch.float64, device="cuda") + 0.5
+        b = torch.arange(nb, dtype=torch.float64, device="cuda") - 3.0
+        a0, b0 = a.clone(), b.clone()
+        code = lib.gna_grad_scale(a.data_ptr() if na else None, na, b.data_ptr() if nb else None, nb, s.data_ptr(),
+                                  stream)
+        assert code == N.GNA_OK
+        assert torch.equal(a, a0 * -2.5) and torch.equal(b, b0 * -2.5), (na, nb)
+
+
 def test_autograd_function(api):
     case = get_case("nuisance_64x1000")
     w = case.w

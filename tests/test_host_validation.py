@@ -53,6 +53,9 @@ def desc(N, **kw):
     (dict(edges=np.linspace(-1.0, 8.0, 11)), EINVAL),                             # E <= 0
     (dict(L=np.array([52.5, 0.0])), EINVAL),
     (dict(Lweight=np.array([1.0, -0.5])), EINVAL),
+    (dict(Lweight=np.array([0.0, 0.0])), EINVAL),                                  # weights normalised by their sum
+    (dict(Lweight=np.array([1.0, float("inf")])), EINVAL),
+    (dict(L=np.array([52.5, float("inf")])), EINVAL),
     (dict(nodes_per_bin=0), ESHAPE),
     (dict(nodes_per_bin=65537), ESHAPE),
     (dict(npts=3, node_counts=np.array([4, 0, 9], dtype=np.int32)), ESHAPE),

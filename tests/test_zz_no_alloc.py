@@ -134,15 +134,19 @@ def test_noalloc_refuses_memory_it_cannot_use():
     P = ctypes.POINTER(ctypes.c_double)
     vp = lambda t, off=0: ctypes.c_void_p(t.data_ptr() + off)
 
-    def call(E_, W_, d_, c_):
-        return N.lib().gna_chain_eval_noalloc(w.nbins, w.nodes_per_bin, E_, W_, Ls.ctypes.data_as(P), Ls.size, None,
-                                              vp(params), ctypes.c_double(case.N), w.kind, d_, c_, None, None, None)
+    def call(E_, W_, d_, c_, lw=None):
+        return N.lib().gna_chain_eval_noalloc(w.nbins, w.nodes_per_bin, E_, W_, Ls.ctypes.data_as(P), Ls.size,
+                                              None if lw is None else lw.ctypes.data_as(P), vp(params),
+                                              ctypes.c_double(case.N), w.kind, d_, c_, None, None, None)
 
     assert call(vp(E), vp(W), vp(data), vp(chi2)) == N.GNA_OK
     torch.cuda.synchronize()
     assert call(vp(host), vp(W), vp(data), vp(chi2)) == N.GNA_EINVAL
     assert call(vp(E, 4), vp(W), vp(data), vp(chi2)) == N.GNA_EINVAL
     assert call(vp(E), vp(W), vp(data), None) == N.GNA_EINVAL
+    # baseline weights are normalised by their sum: zero or infinite ones are refused
+    assert call(vp(E), vp(W), vp(data), vp(chi2), np.zeros(Ls.size)) == N.GNA_EINVAL
+    assert call(vp(E), vp(W), vp(data), vp(chi2), np.full(Ls.size, np.inf)) == N.GNA_EINVAL
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():

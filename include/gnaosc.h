@@ -62,7 +62,9 @@ typedef enum {
 typedef enum {
     GNA_FP64 = 0,           /* all arithmetic in double */
     GNA_MIXED_F64PHASE = 1, /* phase and its reduction mod pi in double, the rest FP32 + Kahan */
-    GNA_MIXED_FFPHASE = 2   /* phase as an unevaluated sum of two floats (double-FP32), rest FP32 + Kahan */
+    GNA_MIXED_FFPHASE = 2   /* phase as an unevaluated sum of two floats (double-FP32), rest FP32 + Kahan;
+                               the reduction is exact for phases below 2^12 pi = 12,868 rad (K dm2 L / E),
+                               beyond that its error grows with the phase: use GNA_MIXED_F64PHASE there */
 } gna_precision;
 
 typedef enum { GNA_PEARSON = 0, GNA_POISSON = 1 } gna_chi2_kind;

@@ -218,8 +218,9 @@ struct NodeMathGen {
 // Q(3): vd = {U, V, Q} (nine values) in double, vf the NV values in FP32, and
 // the point's coefficients.  Each pair's sine sum is U, or sum W sum omega - Q where Q is
 // the smaller sum (see the header); M is formed in double (its
-// terms may cancel), its six derivatives in FP32, then the chi^2 term and its
-// gradient contributions into regs[0..6] (float pairs): [0] the chi^2 term,
+// terms may cancel), its six derivatives in FP32, then the chi^2 term (from
+// d - mu in double and the relative residual in FP32) and its gradient
+// contributions into regs[0..6] (float pairs): [0] the chi^2 term,
 // [1 + q] g_i N (1 + eta_i) dM/dp_q.
 __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int p, int i, const double* vd,
                                         const float* vf, const BinIn& in, float2* regs) {
@@ -236,13 +237,19 @@ __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int
     const double f = a.norm * (1.0 + e);
     const double mu = f * M;
     const double d = in.d;
-    double term, gd;
+    // as in the survival chain's mixed epilogue: d - mu in double (they are
+    // close), the relative residual t = (d - mu) / mu, the Poisson term
+    // 2 mu h(t) and the adjoint in FP32 (1e-7 relative per bin)
+    const double dm = d - mu;
+    const float tf = (float)dm / (float)mu;
+    double term;
+    float g;
     if (a.kind == GNA_PEARSON) {
-        term = (d - mu) * (d - mu) / mu;
-        gd = 1.0 - (d * d) / (mu * mu);
+        term = dm * (double)tf;                // (d - mu)^2 / mu
+        g = 1.0f - (1.0f + tf) * (1.0f + tf);  // 1 - d^2 / mu^2
     } else {
-        term = (d > 0.0) ? 2.0 * (mu - d + d * log(d / mu)) : 2.0 * mu;
-        gd = 2.0 * (1.0 - d / mu);
+        term = (d > 0.0) ? 2.0 * mu * (double)poisson_h(tf) : 2.0 * mu;
+        g = -2.0f * tf;  // 2 (1 - d / mu)
     }
     const bool pen = a.eta && a.sigma > 0.0;
     if (pen) term += e * e / (a.sigma * a.sigma);
@@ -257,7 +264,7 @@ __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int
         const float t31 = fmaf(c.af[1], vf[7], 0.5f * c.bf[1] * vf[10]);
         dM[4] = fmaf(c.af[0], vf[6], fmaf(0.5f * c.bf[0], vf[9], t31));
         dM[5] = fmaf(c.af[2], vf[8], fmaf(0.5f * c.bf[2], vf[11], t31));
-        const float gf = (float)(gd * f);
+        const float gf = g * (float)f;
         for (int q = 0; q < 6; q++) regs[1 + q] = make_float2(gf * dM[q], 0.f);
         if (a.NBV >= kGenNBVFit) {
             // fits: this bin's part of J^T W J, J_q = d mu / d p_q, W = 2 / mu
@@ -270,7 +277,8 @@ __device__ inline void gen_bin_epilogue(const EpiArgs& a, const GenConst& c, int
         }
     }
     if (a.mu_out) a.mu_out[idx] = mu;
-    if (a.grad_eta_out) a.grad_eta_out[idx] = gd * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
+    if (a.grad_eta_out)
+        a.grad_eta_out[idx] = (double)g * a.norm * M + (pen ? 2.0 * e / (a.sigma * a.sigma) : 0.0);
 }
 
 // Group g of point p: lane l holds the values of bin 32 g + l in regs; up to

@@ -59,12 +59,17 @@ def test_gl_nodes(api, n):
 
 # ------------------------------------------------------------------ OscProb
 @pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
-@pytest.mark.parametrize("rng_case", ["reactor", "long_baseline"])
+@pytest.mark.parametrize("rng_case", ["reactor", "long_baseline", "largest_phases"])
 def test_oscprob(api, prec, rng_case):
     rng = np.random.default_rng(11)
     if rng_case == "reactor":
         E = rng.uniform(0.5, 15.0, 100003)
         L = [0.5, 52.5, 60.0, 17.3]
+    elif rng_case == "largest_phases":
+        # reactor energies across the Earth: Delta_31 up to 9.4e3 rad, near
+        # the 12,868 rad below which the double-float phase's reduction is exact
+        E = rng.uniform(1.8, 15.0, 100003)
+        L = [3000.0, 5200.0]
     else:
         E = rng.uniform(500.0, 5000.0, 4099)
         L = [810.0]

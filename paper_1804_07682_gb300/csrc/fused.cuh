@@ -377,8 +377,18 @@ __global__ void __launch_bounds__(256) k_fused_bins(BinArgs a) {
         float2 regs[15];  // this lane's per-bin values: the warp reduces its own group
         if (i < a.nbins) {
             double v[NV];
+            if constexpr (NL == 1) {
+                // one baseline (the scans): the tangent sums rounded once to
+                // FP32 (the epilogue uses them in FP32), the rest in double
+                constexpr int T1 = GRAD ? 5 : 1;
 #pragma unroll
-            for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
+                for (int j = 0; j < NV; j++)
+                    v[j] = (j >= 1 && j < T1) ? (double)__fsub_rn(acc[j].s, acc[j].c)
+                                              : (double)acc[j].s - (double)acc[j].c;
+            } else {
+#pragma unroll
+                for (int j = 0; j < NV; j++) v[j] = (double)acc[j].s - (double)acc[j].c;
+            }
             bin_epilogue(a.ea, p, i, v, bin_inputs(a.ea, p, i), regs);
         }
         group_done(a.ea, p, b, lane, regs);

@@ -78,8 +78,8 @@ PROFILE_EVERY = 8
 TRAFFIC_CAPTURE = {
     "split": {"sources_sha256": "4e84d90634a932986bddfc3627e81e2c61c0ee248b37d8a2b42cd44e71396f94",
               "bytes": 265113600 + 4114176},
-    "slices": {"sources_sha256": "f93aba906a80d2c87008e758f7b0bee1995e094b4aac781b09367e9adf452104",
-               "bytes": 268572160 + 4480000 + 8177408 + 0},
+    "slices": {"sources_sha256": "ee1c2edc308edbe2ecc5ca374d8666315fc1bb510abdc327df76998aaec7e7e2",
+               "bytes": 268506880 + 4611584 + 8178176 + 0},
 }
 KERNEL_SOURCES = ["paper_1804_07682_gb300/csrc/common.cuh", "paper_1804_07682_gb300/csrc/fused.cuh",
                   "paper_1804_07682_gb300/csrc/epilogue.cuh", "paper_1804_07682_gb300/csrc/ff_consts.h",

@@ -613,6 +613,7 @@ class OscChi2(torch.autograd.Function):
         return chi2
 
     @staticmethod
+    @torch.autograd.function.once_differentiable
     def backward(ctx, go):
         # the kept gradient is scaled by grad_output in place, one launch for
         # theta and eta (gna_grad_scale), and handed to the gradient

@@ -600,6 +600,11 @@ def test_autograd_function(api):
     api.chi2(theta, plan, d, eta, w.sigma_eta).backward()
     assert normrel(theta.grad.cpu().numpy(), 3.0 * ref["grad"][:4]) < 1e-9
     assert normrel(eta.grad.cpu().numpy(), 3.0 * ref["grad"][4:]) < 1e-9
+    # first derivatives only: differentiating the gradient again is refused
+    (gth,) = torch.autograd.grad(api.chi2(theta, plan, d, eta, w.sigma_eta), theta, create_graph=True)
+    assert normrel(gth.detach().cpu().numpy(), ref["grad"][:4]) < 1e-9
+    with pytest.raises(RuntimeError):
+        gth.sum().backward()
 
     # FP64 central differences (h = 1e-6 relative) through the same plan
     def f(t):

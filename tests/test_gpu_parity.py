@@ -46,7 +46,7 @@ def make_plan(api, case, prec, mapping=None, with_plain=False, per_point_data=Fa
 
 
 # ------------------------------------------------------------ Gauss-Legendre
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 50, 262, 524, 4096, 16384])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 50, 262, 524, 4096, 16384, 65536])
 def test_gl_nodes(api, n):
     x, w = api.gl_nodes(n)
     xr, wr = oracle.gl(n)

@@ -52,8 +52,13 @@ def test_gl_nodes(api, n):
     xr, wr = oracle.gl(n)
     x = x.cpu().numpy()
     assert np.abs(x - xr).max() < 2e-15
-    # a one-ulp difference in a node moves its weight by ~4|x|/(1-x^2) ulp
-    tol = 1e-12 + 4 * np.spacing(1.0) * np.abs(xr) / ((1 - xr) * (1 + xr))
+    # a one-ulp difference in a node moves its weight by ~4|x|/(1-x^2) ulp;
+    # the weight needs P_n' from an n-step three-term recurrence, which the
+    # two sides round differently (up to ~n ulp: at n = 65536 the oracle and
+    # a float64 replay of the kernel's recurrence are within 8e-12 of 40-digit
+    # weights at sampled nodes, and the two sides measured 4.8e-12 apart)
+    eps = np.spacing(1.0)
+    tol = 1e-12 + n * eps + 4 * eps * np.abs(xr) / ((1 - xr) * (1 + xr))
     assert np.all(np.abs(w.cpu().numpy() / wr - 1) <= tol)
 
 

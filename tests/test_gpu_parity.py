@@ -372,6 +372,20 @@ def test_one_bin_of_many_nodes(api, prec, mapping):
     check_chain(api, Case(w), prec, mapping, plain_chi2=(prec == "fp64"))
 
 
+_largest = {}
+
+
+@pytest.mark.parametrize("prec,mapping", [("fp64", None), ("ff", "slices"), ("ff", "bins")])
+def test_one_bin_of_the_largest_order(api, prec, mapping):
+    # the same bin at the largest Gauss-Legendre order a plan accepts (65536
+    # nodes): grid build at that order and the longest node loops; chi^2 as
+    # in the 16384-node case (scaled bound in the mixed modes)
+    if "case" not in _largest:
+        w = wl.shrink(wl.reactor8_1000x16384(), nbins=1)
+        _largest["case"] = Case(wl.Workload("one_bin_65536", w.edges, 65536, w.L, w.theta, w.kind))
+    check_chain(api, _largest["case"], prec, mapping, plain_chi2=(prec == "fp64"))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
 def test_points_sharing_grids(api, prec):
     # points with equal node counts share one energy grid on the device; the

@@ -469,10 +469,11 @@ gna_status gna_fp32_probe(int blocks, int iters, float* out, void* stream);
  * a function of chi^2 (an autograd engine): with s = d loss / d chi^2 on the
  * device, a[i] *= *s for i < na and b[j] *= *s for j < nb, in place, in one
  * launch on `stream` (a = d chi2 / d theta, b = d chi2 / d eta as an
- * evaluation wrote them).  a, b, s: device memory of the current device,
- * float64, owned by the caller; a (b) may be NULL when na (nb) is 0.
- * GNA_EINVAL for s == NULL, negative counts or a NULL array with a positive
- * count; GNA_ECUDA if the launch fails. */
+ * evaluation wrote them).  a, b, s: memory the current device can access,
+ * float64 (8-byte aligned), owned by the caller; a (b) may be NULL when na
+ * (nb) is 0; na = nb = 0 launches nothing.  GNA_EINVAL for s == NULL,
+ * negative counts, a NULL array with a positive count, or memory the
+ * device cannot access; GNA_ECUDA if the launch fails. */
 gna_status gna_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s, void* stream);
 
 

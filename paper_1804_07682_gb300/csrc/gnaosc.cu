@@ -1726,6 +1726,11 @@ gna_status gna_fp32_probe(int blocks, int iters, float* out, void* stream) {
 gna_status gna_grad_scale(double* a, int64_t na, double* b, int64_t nb, const double* s, void* stream) {
     if (!s || na < 0 || nb < 0 || (na > 0 && !a) || (nb > 0 && !b) || na > INT64_MAX / 2 || nb > INT64_MAX / 2)
         return GNA_EINVAL;
+    if (na + nb == 0) return GNA_OK;
+    // memory the current device cannot read or write is refused before a launch could fault
+    if (!device_accessible(s) || !aligned(s, sizeof(double))) return GNA_EINVAL;
+    if (na > 0 && (!device_accessible(a) || !aligned(a, sizeof(double)))) return GNA_EINVAL;
+    if (nb > 0 && (!device_accessible(b) || !aligned(b, sizeof(double)))) return GNA_EINVAL;
     return launch_grad_scale(a, na, b, nb, s, (cudaStream_t)stream) == cudaSuccess ? GNA_OK : GNA_ECUDA;
 }
 

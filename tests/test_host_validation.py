@@ -169,5 +169,7 @@ def test_grad_scale_refuses_bad_arguments(N):
     buf = (ctypes.c_double * 4)()
     assert L.gna_grad_scale(ctypes.addressof(buf), -1, None, 0, ctypes.addressof(s), None) == EINVAL
     assert L.gna_grad_scale(ctypes.addressof(buf), 4, ctypes.addressof(buf), -2, ctypes.addressof(s), None) == EINVAL
+    # host memory no device can reach (here: no GPU at all) is refused before any launch
+    assert L.gna_grad_scale(ctypes.addressof(buf), 4, None, 0, ctypes.addressof(s), None) == EINVAL
     # nothing to scale: no launch, success
     assert L.gna_grad_scale(None, 0, None, 0, ctypes.addressof(s), None) == OK

@@ -807,6 +807,31 @@ def test_general_chain_uneven_grids_baselines_nuisances(api, channel, prec):
                   4, 1e-3, 0, 9, nuisances=True, uniform=False)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("prec", ["ff", "fp64"])
+def test_general_chain_sparse_counts(api, prec, kind):
+    # 200 nu_mu -> nu_e events over 40 bins: Poisson data with empty bins
+    # (the d = 0 terms of both chi^2 kinds) and mu of a few events per bin
+    edges = np.linspace(500.0, 5000.0, 41)
+    n, L = 16, np.array([810.0])
+    mu_rb, _ = oracle.binned_general(edges, n, L, GEN_TH, "mu", "e", False, 1e-3)
+    N = 200.0 / mu_rb[0].sum()
+    data = wl.poisson_data(N * mu_rb[0], 123)
+    assert np.any(data == 0)
+    theta = GEN_TH * np.array([1.02, 0.98, 1.01, 0.97, 1.03, 0.99])
+    ref = oracle.chain_general(edges, n, L, theta, N, data, "mu", "e", False, kind, None, 0.0, 1e-3)
+    plan = api.Plan(edges, L, nodes_per_bin=n, norm=N, e_scale=1e-3, prec=prec, kind=KIND_NAMES[kind],
+                    channel=("mu", "e", False))
+    out = plan.eval_general(plan.params_tensor(theta[None, :]), dev(data), grad=True, mu=True)
+    torch.cuda.synchronize()
+    plan.status()
+    tol, gtol = (1e-9, 1e-9) if prec == "fp64" else (1e-6, 1e-4)
+    check_chi2(out["chi2"][0].item(), ref, data, kind, tol, tag="general sparse %s %d" % (prec, kind))
+    assert rel(out["mu"][0].cpu().numpy(), ref["mu"]) < tol
+    assert normrel(out["grad"][0].cpu().numpy(), ref["grad"][:6]) < gtol
+    plan.close()
+
+
 def test_general_chain_reactor_many_nodes(api):
     # nue_bar survival through the any-channel chain on a reactor-like grid of
     # 20 bins x 2048 nodes and eight baselines (slices of the nodes)

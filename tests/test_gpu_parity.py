@@ -324,6 +324,22 @@ def test_chain_degenerate_shapes(api):
         check_chain(api, case2, prec)
 
 
+@pytest.mark.parametrize("kind", [wl.PEARSON, wl.POISSON])
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
+def test_chain_sparse_counts(api, prec, kind):
+    # 300 events over the 200 reactor bins (8 baselines): Poisson data with
+    # many empty bins (the d = 0 terms of both chi^2 kinds)
+    w = wl.Workload("sparse", np.linspace(1.8, 12.0, 201), 50, wl.reactor8_1000x16384().L,
+                    np.array([wl.TRUTH]) * np.array([[1.02, 0.97, 1.01, 0.99]]), kind)
+    case = Case(w)
+    scale = 300.0 / case.mu_truth.sum()
+    case.N *= scale
+    case.mu_truth = case.mu_truth * scale
+    case.data = wl.poisson_data(case.mu_truth, 77)
+    assert np.sum(case.data == 0) > 20
+    check_chain(api, case, prec)
+
+
 @pytest.mark.parametrize("mapping", ["split", "bins", "slices"])
 @pytest.mark.parametrize("nbins,n,npts", [(1, 8, 40), (3, 5, 50), (2, 16, 3), (7, 3, 33), (2, 40, 3)])
 def test_grids_shorter_than_a_warp(api, nbins, n, npts, mapping):

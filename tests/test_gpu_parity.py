@@ -324,6 +324,18 @@ def test_chain_degenerate_shapes(api):
         check_chain(api, case2, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
+def test_chain_boundary_parameters(api, prec):
+    # points on the edges of the physical domain: theta13 = 0 (two-flavour
+    # limit), theta12 = 0 and 90 degrees, dm2_21 = 0, theta13 = 90 degrees
+    # (P = 1), and a vanishing dm2_32; reactor bins, eight baselines
+    t = wl.TRUTH
+    theta = np.array([[t[0], 0.0, t[2], t[3]], [0.0, t[1], t[2], t[3]], [1.0, t[1], t[2], t[3]],
+                      [t[0], t[1], 0.0, t[3]], [t[0], 1.0, t[2], t[3]], [t[0], t[1], t[2], 1e-9]])
+    w = wl.Workload("boundary", np.linspace(1.8, 12.0, 41), 24, wl.reactor8_1000x16384().L, theta, wl.POISSON)
+    check_chain(api, Case(w), prec)
+
+
 @pytest.mark.parametrize("kind", [wl.PEARSON, wl.POISSON])
 @pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
 def test_chain_sparse_counts(api, prec, kind):

@@ -860,6 +860,36 @@ def test_general_chain_sparse_counts(api, prec, kind):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["ff", "fp64"])
+def test_general_chain_boundary_parameters(api, prec):
+    # any-channel coefficients next to the edges of the domain (a plan
+    # reports a sin^2 at exactly 0 or 1 as outside it: the mixing matrix
+    # holds square roots, whose derivatives diverge there): theta13 -> 0,
+    # theta23 -> 0 and 90 degrees, theta12 -> 90 degrees, and the
+    # CP-conserving delta = 0 and pi; nu_mu -> nu_e at 810 km
+    edges = np.linspace(500.0, 5000.0, 41)
+    n, L = 16, np.array([810.0])
+    g, e = GEN_TH, 1e-10
+    theta = np.array([[g[0], e, g[2], g[3], g[4], g[5]], [g[0], g[1], e, g[3], g[4], g[5]],
+                      [g[0], g[1], 1.0 - e, g[3], g[4], g[5]], [g[0], g[1], g[2], 0.0, g[4], g[5]],
+                      [1.0 - e, g[1], g[2], g[3], g[4], g[5]], [g[0], g[1], g[2], np.pi, g[4], g[5]]])
+    mu_rb, _ = oracle.binned_general(edges, n, L, GEN_TH, "mu", "e", False, 1e-3)
+    N = 1e4 / mu_rb[0].sum()
+    data = wl.poisson_data(N * mu_rb[0], 5)
+    plan = api.Plan(edges, L, npts=theta.shape[0], nodes_per_bin=n, norm=N, e_scale=1e-3, prec=prec, kind="poisson",
+                    channel=("mu", "e", False))
+    out = plan.eval_general(plan.params_tensor(theta), dev(data), grad=True, mu=True)
+    torch.cuda.synchronize()
+    plan.status()
+    tol, gtol = (1e-9, 1e-9) if prec == "fp64" else (1e-6, 1e-4)
+    for p in range(theta.shape[0]):
+        ref = oracle.chain_general(edges, n, L, theta[p], N, data, "mu", "e", False, 1, None, 0.0, 1e-3)
+        check_chi2(out["chi2"][p].item(), ref, data, 1, tol, tag="general boundary %s p%d" % (prec, p))
+        assert rel(out["mu"][p].cpu().numpy(), ref["mu"]) < tol, p
+        assert normrel(out["grad"][p].cpu().numpy(), ref["grad"][:6]) < gtol, p
+    plan.close()
+
+
 def test_general_chain_reactor_many_nodes(api):
     # nue_bar survival through the any-channel chain on a reactor-like grid of
     # 20 bins x 2048 nodes and eight baselines (slices of the nodes)

@@ -890,6 +890,22 @@ def test_general_chain_boundary_parameters(api, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("mapping", [None, "bins"])
+def test_general_repeated_evaluations_are_bit_identical(api, mapping):
+    # the any-channel chain's sums (node, slice, group, point) also run in a
+    # fixed order: repeated evaluations agree bit for bit
+    theta, counts, N, data, eta, refs = general_case(("mu", "e", False), np.linspace(500.0, 5000.0, 41), 64,
+                                                     np.array([810.0, 790.0]), 3, 1e-3, 1, 21)
+    plan = api.Plan(np.linspace(500.0, 5000.0, 41), [810.0, 790.0], npts=3, nodes_per_bin=64, norm=N, e_scale=1e-3,
+                    prec="ff", kind="poisson", channel=("mu", "e", False), mapping=mapping)
+    p, d = plan.params_tensor(theta), dev(data)
+    outs = [{k: v.clone() for k, v in plan.eval_general(p, d, grad=True, mu=True).items()} for _ in range(5)]
+    for o in outs[1:]:
+        for k in o:
+            assert torch.equal(o[k], outs[0][k]), k
+    plan.close()
+
+
 def test_general_chain_reactor_many_nodes(api):
     # nue_bar survival through the any-channel chain on a reactor-like grid of
     # 20 bins x 2048 nodes and eight baselines (slices of the nodes)

@@ -672,7 +672,7 @@ def test_autograd_function(api):
     assert tuple(th2.grad.shape) == (1, 4) and normrel(th2.grad[0].cpu().numpy(), ref0["grad"][:4]) < 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp64", "ff"])
+@pytest.mark.parametrize("prec", ["fp64", "f64phase", "ff"])
 def test_fits_match_oracle(api, prec):
     case = get_case("fits_8x100x20")
     w = case.w
@@ -689,7 +689,7 @@ def test_fits_match_oracle(api, prec):
         pull = float(np.max(np.abs(P[j] - th) / fit_sigma(ev(th))))
         log_err("fit %s" % prec, chi2_rel=rel(C[j], c2), params_rel=rel(P[j], th), pull=pull)
         assert rel(C[j], c2) < (1e-9 if prec == "fp64" else 1e-6), (j, C[j], c2)
-        # mixed: largest measured 7.7e-6 relative
+        # mixed: largest measured 7.7e-6 relative (5.1e-5 with the double phase)
         assert rel(P[j], th) < (1e-7 if prec == "fp64" else 1e-4), (j, P[j], th)
         # in units of the parameters' statistical errors the two fits agree far
         # inside any physics resolution
